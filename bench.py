@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark: Viola-Jones AdaBoost training throughput (boosting rounds/s) on GB300.
+
+One step = one whole training job on the 24x24 / 15,000-window workload
+(5,000 faces, 10,000 non-faces, synthetic): load the windows, integral images,
+all 162,336 Haar features evaluated and sorted, then 200 boosting rounds, each
+a search over every feature, polarity and threshold plus the reweighting.
+value = rounds of all jobs / time, with the windows already in HBM when the
+timed region starts.  e2e = the same through the C ABI from host buffers
+(windows copied in, stumps copied out, inside the timed region).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Under torchrun (N > 1) every rank trains its own job on its own GPU
+(replicas: the method has no exchange step on one GPU); the slowest rank's
+time is used.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "boosting rounds/s at 24x24, 15k samples"
+STUMP_BYTES = 40
+PROFILE = os.path.join(ROOT, "profiles", "k_screen_paper_24x24_15k.txt")
+SEARCH_SRC = os.path.join(ROOT, "paper_1306_1467_gb300", "csrc", "k_search.cu")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="paper_24x24_15k")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic():
+    """DRAM bytes per search launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    try:
+        sha = hashlib.sha256(open(SEARCH_SRC, "rb").read()).hexdigest()
+        kv = {}
+        for line in open(PROFILE):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") != sha:
+            return None
+        return float(kv["dram_bytes_per_launch"])
+    except Exception:
+        return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.uuid:
+                cmd += ["-i", self.uuid]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 8:
+                    continue
+                try:
+                    sm.append(float(parts[0]))
+                    smax.append(float(parts[1]))
+                except ValueError:
+                    continue
+                for name, flag in zip(names, parts[4:8]):
+                    if flag.lower() in ("active", "1", "0x1"):
+                        reasons.add(name)
+            os.unlink(self.path)
+        except Exception:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_baseline(px, y, rounds: int, every: int = 8, sample_rounds: int = 3):
+    """The CPU oracle as it stands, on a bounded sample of the workload: every
+    `every`-th feature, its values, value orders and `sample_rounds` rounds;
+    the job time is scaled to all features and `rounds` rounds."""
+    import numpy as np
+
+    import oracle as O
+    n, H, W = px.shape
+    desc, _ = O.haar_enumerate(W, H)
+    sub = desc[::every]
+    t0 = time.perf_counter()
+    ii = O.integral(px)
+    vals = O.feature_values(px, sub, ii)
+    order = O.sort_rows(vals)
+    t1 = time.perf_counter()
+    w = O.initial_weights(y)
+    for _ in range(sample_rounds):
+        st, s, w = O.round_step(vals, order, y, w)
+    t2 = time.perf_counter()
+    scale = desc.shape[0] / sub.shape[0]
+    prep_s = (t1 - t0) * scale
+    round_s = (t2 - t1) / sample_rounds * scale
+    job_s = prep_s + rounds * round_s
+    del np
+    return {"value": rounds / job_s, "unit": "rounds/s", "cores": O.num_threads(), "kind": "oracle",
+            "sample": (f"every {every}th feature ({sub.shape[0]} of {desc.shape[0]}), all {n} windows: "
+                       f"values + stable sort + {sample_rounds} FP64 rounds, scaled to all features "
+                       f"and {rounds} rounds"),
+            "job_s": job_s, "prep_s": prep_s, "round_s": round_s, "measured_s": t2 - t0}
+
+
+def run_reference(a, ws, rank):
+    if rank != 0:
+        return
+    from paper_1306_1467_gb300 import synth
+    px, y, rounds = synth.workload(a.workload)
+    for _ in range(a.warmup):
+        cpu_baseline(px, y, rounds, every=32, sample_rounds=1)
+    vals = [cpu_baseline(px, y, rounds, every=32, sample_rounds=1) for _ in range(a.steps)]
+    v = statistics.median([x["value"] for x in vals])
+    ms = 1000.0 * rounds / v
+    measured_ms = 1000.0 * statistics.median([x["measured_s"] for x in vals])
+    line = {"metric": METRIC, "value": v, "unit": "rounds/s", "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": a.workload, "rounds_per_step": rounds},
+            "cpu_baseline": {"value": v, "unit": "rounds/s", "kind": "oracle", "cores": vals[0]["cores"],
+                             "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": "rounds/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "note": ("ms_per_step is the whole job extrapolated from the sample; "
+                     f"each step measured {measured_ms:.0f} ms of oracle work")}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(a, ws, rank, local):
+    import numpy as np
+    import torch
+
+    from paper_1306_1467_gb300 import synth, vjb
+
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    cfg = dict(synth.WORKLOADS[a.workload])
+    rounds = cfg.pop("rounds")
+    cfg["seed"] = cfg["seed"] + 1000 * rank  # replicas train independent jobs
+    px, y = synth.make_windows(**cfg)
+    n, H, W = px.shape
+    stream = torch.cuda.Stream(device=dev)
+    d_px = torch.from_numpy(px).to(dev)
+    d_y = torch.from_numpy(y).to(dev)
+    torch.cuda.synchronize()
+    tr = vjb.Trainer(local, stream=stream.cuda_stream)
+
+    def job(host: bool):
+        if host:
+            tr.load_windows(px, y)
+        else:
+            tr.load_windows(d_px, d_y)
+        tr.build_integral()
+        nf = tr.feature_count()
+        st, stumps = tr.train_strong(rounds)
+        assert st == vjb.OK and len(stumps) == rounds, (st, len(stumps))
+        return nf, stumps
+
+    for _ in range(max(a.warmup, 1)):
+        nf, _ = job(False)
+    info0 = tr.info()
+    tr.set_timing(True)
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(dev).uuid)
+        if not uuid.startswith("GPU-"):
+            uuid = "GPU-" + uuid
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        job(False)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    tm = tr.timing()
+    info1 = tr.info()
+    launches = info1["launches"] - info0["launches"]
+    tr.set_timing(False)
+
+    # setup vs rounds split of one job (extra run, untimed for `value`)
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s2 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    tr.load_windows(d_px, d_y)
+    tr.build_integral()
+    tr.feature_count()
+    s1.record(stream)
+    tr.train_strong(rounds)
+    s2.record(stream)
+    s2.synchronize()
+    setup_ms, rounds_ms = s0.elapsed_time(s1), s1.elapsed_time(s2)
+
+    e2e = None
+    if not a.no_e2e:
+        job(True)  # warm the host path
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        h0.record(stream)
+        t_host = time.perf_counter()
+        for _ in range(a.steps):
+            job(True)
+        h1.record(stream)
+        h1.synchronize()
+        host_s = time.perf_counter() - t_host
+        e2e_ms = max(h0.elapsed_time(h1), 1000.0 * host_s)
+        e2e = {"value": None, "unit": "rounds/s", "h2d_bytes_per_step": int(px.nbytes + y.nbytes),
+               "d2h_bytes_per_step": int(rounds * STUMP_BYTES), "ms_per_step": e2e_ms / a.steps,
+               "_ms": e2e_ms}
+
+    if dist:
+        t = torch.tensor([ms, e2e["_ms"] if e2e else 0.0], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+        if e2e:
+            e2e["_ms"] = float(t[1])
+    total_rounds = ws * a.steps * rounds
+    value = total_rounds / (ms / 1000.0)
+    if e2e:
+        e2e["value"] = total_rounds / (e2e.pop("_ms") / 1000.0)
+
+    search_bytes = 2.0 * nf * n
+    avg_search_ms = tm["search_ms_total"] / max(tm["rounds"], 1)
+    achieved = search_bytes / (avg_search_ms / 1000.0) / 1e9
+    peak, peak_src = _peak()
+    traffic = _traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "rounds/s", "n_gpus": ws, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": a.workload, "window": f"{W}x{H}", "samples": n,
+                   "positives": int(y.sum()), "negatives": int(n - y.sum()), "features": nf,
+                   "rounds_per_step": rounds,
+                   "step": "load windows + integral images + feature values + sort + rounds",
+                   "l2": f"inputs larger than L2: the {search_bytes / 1e9:.2f} GB sorted table is read every round",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "search_shape": {"warps": info1["kernel_warps"], "stages": info1["kernel_stages"],
+                                    "ctas": info1["kernel_ctas"]}},
+        "roofline": {"kernel": "k_screen", "bound": "hbm", "achieved": achieved, "peak": peak,
+                     "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": traffic, "algorithmic_bytes_per_launch": search_bytes,
+                     "avg_launch_ms": avg_search_ms, "min_launch_ms": tm["search_ms_min"],
+                     "max_launch_ms": tm["search_ms_max"], "launches_timed": tm["rounds"]},
+        "gpu_launches": int(launches),
+        "rounds_only_per_s": 1000.0 * rounds / rounds_ms,
+        "setup_ms": setup_ms,
+        "round_ms": tm["round_ms_total"] / max(tm["rounds"], 1),
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if ck:
+        line["clocks"] = ck
+    if ws == 1 and rank == 0 and not a.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(px, y, rounds)
+    tr.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    del np
+
+
+def main():
+    a = _args()
+    ws, rank, local = _dist()
+    if a.impl == "reference":
+        run_reference(a, ws, rank)
+    else:
+        run_ours(a, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

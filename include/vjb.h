@@ -1,0 +1,230 @@
+/*
+ * vjb.h -- C ABI of the GB300 (sm_103a) Viola-Jones AdaBoost trainer.
+ *
+ * The library trains the discrete AdaBoost of Viola and Jones over the full
+ * Haar feature set of a window, as restated in Abualkibash, ElSayed and
+ * Mahmood, "Highly scalable, parallel and distributed AdaBoost algorithm using
+ * light weight threads and web services on a network of multi-core machines"
+ * (arXiv 1306.1467), Sec. 2.  Every step of a round runs in the library's own
+ * CUDA kernels on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - Return value: VJB_OK (0), a positive VJB_DONE_* status, or a negative
+ *     error code.  On a negative code nothing visible to the caller has
+ *     changed except where noted, and vjb_last_error() gives a message.
+ *   - Pointers named "host" are ordinary host memory owned by the caller; the
+ *     library copies from / into them before returning and keeps no
+ *     reference.  Pointers named "device" are device memory on the context's
+ *     device, owned by the caller, read before the call returns.
+ *   - All device memory the library needs is allocated by the context and
+ *     released by vjb_destroy().
+ *   - Calls on one context must not overlap (one host thread at a time).
+ *     Every call is synchronous with respect to the context's stream.
+ */
+#ifndef VJB_H
+#define VJB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------- */
+#define VJB_OK            0
+#define VJB_DONE_PERFECT  1   /* eps == 0: stump kept (alpha = +inf), training over   */
+#define VJB_DONE_NOGAIN   2   /* eps >= 1/2: stump not kept, training over            */
+#define VJB_EINVAL      (-1)  /* bad argument (sizes, labels, ranges)                 */
+#define VJB_ESTATE      (-2)  /* call out of order                                    */
+#define VJB_ENOMEM      (-3)  /* device allocation failed                             */
+#define VJB_ECUDA       (-4)  /* CUDA runtime / driver error                          */
+#define VJB_EDEVICE     (-5)  /* a kernel set its error flag (wait timeout, bounds)   */
+
+/* Limits.  Sample indices are stored in 15 bits and index N marks padding. */
+#define VJB_MAX_SAMPLES 32766
+#define VJB_MAX_WINDOW  255
+
+/* Haar feature types in canonical order (Sec. 2.2 lists them in this order). */
+#define VJB_HAAR_3H 0   /* three rectangles side by side along x, base 3x1 */
+#define VJB_HAAR_3V 1   /* three rectangles stacked along y,      base 1x3 */
+#define VJB_HAAR_2H 2   /* two rectangles side by side along x,   base 2x1 */
+#define VJB_HAAR_2V 3   /* two rectangles stacked along y,        base 1x2 */
+#define VJB_HAAR_4  4   /* two by two rectangles,                 base 2x2 */
+
+typedef struct vjb_ctx vjb_ctx;
+
+/* One Haar feature: its top-left corner (x, y) and full size (w, h) in pixels.
+ * Value (Sec. 2.2, dark minus white): 2H/2V = S(right|bottom) - S(left|top);
+ * 3H/3V = S(middle) - S(first) - S(last); 4 = S(top-right) + S(bottom-left)
+ * - S(top-left) - S(bottom-right). */
+typedef struct {
+    uint8_t type, x, y, w, h;
+} vjb_feature;
+
+/* One weak classifier h(x) = 1 iff polarity * f(x) < polarity * threshold
+ * (Sec. 2.2), with its round's weighted error (Sec. 2.3 step 2),
+ * beta = error / (1 - error) and alpha = log(1 / beta) (Sec. 2.3). */
+typedef struct {
+    int32_t feature;    /* index into the canonical feature list          */
+    int32_t threshold;  /* integer threshold theta                        */
+    int32_t polarity;   /* +1 or -1                                       */
+    int32_t split;      /* samples on the "below" side in value order     */
+    double  error;      /* weighted error, FP64 sum over the samples      */
+    double  beta;
+    double  alpha;      /* +inf when error == 0                           */
+} vjb_stump;
+
+/* Diagnostics of the context and of its last search. */
+typedef struct {
+    int32_t n, h, w;          /* samples and window size                        */
+    int32_t npad;             /* sorted-table row length (samples padded)       */
+    int64_t features;         /* F                                              */
+    int32_t rounds_done;      /* stumps kept so far                             */
+    int32_t status;           /* VJB_OK or VJB_DONE_*                           */
+    double  t_pos, t_neg;     /* FP64 class totals of the current weights       */
+    double  weight_sum;       /* FP64 sum of the current FP32 weights           */
+    float   screen_min;       /* smallest FP32 screened error of the last search */
+    int32_t candidates;       /* features re-scanned compensated in that search */
+    int32_t device_flags;     /* error flags set by kernels (0 = none)          */
+    int32_t kernel_warps;     /* search kernel: consumer warps per CTA          */
+    int32_t kernel_stages;    /* search kernel: TMA stages per warp             */
+    int32_t kernel_ctas;      /* search kernel: CTAs in the grid                */
+    int32_t pad;
+    double  search_bytes;     /* algorithmic bytes one search reads: 2 * F * N  */
+    int64_t launches;         /* kernels this context has launched so far       */
+} vjb_info;
+
+/* Per-launch timing of the rounds run since timing was (re)enabled, from CUDA
+ * events recorded on the context's stream around the search kernel and around
+ * the whole round (also inside the CUDA graph that vjb_train_strong replays). */
+typedef struct {
+    int32_t rounds;           /* rounds timed                                   */
+    int32_t pad;
+    double  search_ms_total;  /* sum of search-kernel durations                 */
+    double  search_ms_min;
+    double  search_ms_max;
+    double  round_ms_total;   /* sum of whole-round durations                   */
+} vjb_timing;
+
+/* ---- context ----------------------------------------------------------
+ * vjb_create: make a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t (may be NULL: the context creates its own non-blocking
+ * stream).  *out receives the context.  Errors: VJB_EINVAL (out NULL,
+ * device out of range), VJB_ECUDA. */
+int vjb_create(vjb_ctx **out, int device, void *cuda_stream);
+
+/* Release every device buffer of the context and the context itself.  NULL is
+ * accepted. */
+void vjb_destroy(vjb_ctx *ctx);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *vjb_last_error(void);
+
+/* ---- step 0: training set (Sec. 2.3, Table 1) ---------------------------
+ * vjb_load_windows: copy n windows of h x w uint8 pixels, row-major
+ * [n][h][w] (host), and n labels (host, 1 = face, 0 = non-face) to the
+ * device.  Sets the initial weights of Table 2: 1/(2l) for each of the l
+ * faces, 1/(2m) for each of the m non-faces, normalised in FP64 and stored
+ * FP32.  Discards any earlier training set and its tables.
+ * Errors: VJB_EINVAL if n < 2 or n > VJB_MAX_SAMPLES, h or w outside
+ * [1, VJB_MAX_WINDOW], a label not 0/1, or no face or no non-face;
+ * VJB_ENOMEM; VJB_ECUDA. */
+int vjb_load_windows(vjb_ctx *ctx, const uint8_t *pixels, const uint8_t *labels,
+                     int32_t n, int32_t h, int32_t w);
+
+/* Same as vjb_load_windows with `pixels` and `labels` in device memory. */
+int vjb_load_windows_device(vjb_ctx *ctx, const uint8_t *pixels, const uint8_t *labels,
+                            int32_t n, int32_t h, int32_t w);
+
+/* ---- step 1: integral images (Sec. 2.1) --------------------------------
+ * ii(x, y) = sum of pixels at x' < x, y' < y, with a zero first row and
+ * column, for every window.  Errors: VJB_ESTATE before load; VJB_ECUDA. */
+int vjb_build_integral(vjb_ctx *ctx);
+
+/* ---- step 2: Haar features (Sec. 2.2) ----------------------------------
+ * Enumerate every feature of the window in canonical order (types 3H, 3V,
+ * 2H, 2V, 4; inside a type by width, height, y, x ascending), evaluate every
+ * feature on every window from its integral image (int32, exact), and build
+ * the per-feature sample order used by every round: samples sorted by value,
+ * ties by sample index.  *count receives F.  If `out` is not NULL it must
+ * hold F entries (host) and receives the feature list.  A second call returns
+ * the same list without recomputing.  Errors: VJB_ESTATE before
+ * vjb_build_integral; VJB_EINVAL (count NULL); VJB_ENOMEM; VJB_ECUDA. */
+int vjb_enumerate_haar(vjb_ctx *ctx, int64_t *count, vjb_feature *out);
+
+/* ---- step 3: one boosting round (Sec. 2.3 steps 1-4) --------------------
+ * Normalised weights -> the stump (f, p, theta) of least weighted error over
+ * every feature, polarity and threshold -> beta, alpha -> reweight
+ * w <- w * beta^(1 - e) and renormalise (FP64 total, FP32 storage).
+ * *out (host, may be NULL) receives the stump.  Returns VJB_OK,
+ * VJB_DONE_PERFECT (stump kept, no update) or VJB_DONE_NOGAIN (stump not
+ * kept, no update); once training is over further rounds return the same
+ * status and do nothing.  Errors: VJB_ESTATE before vjb_enumerate_haar;
+ * VJB_EDEVICE; VJB_ECUDA. */
+int vjb_train_round(vjb_ctx *ctx, vjb_stump *out);
+
+/* T rounds, replayed as a CUDA graph with one host synchronisation at the
+ * end.  out (host, T entries, may be NULL) receives the kept stumps;
+ * *rounds_done (may be NULL) how many were kept by this call.  Returns the
+ * status of the last round run.  Errors as vjb_train_round, VJB_EINVAL if
+ * T < 0. */
+int vjb_train_strong(vjb_ctx *ctx, int32_t T, vjb_stump *out, int32_t *rounds_done);
+
+/* ---- state access --------------------------------------------------------
+ * vjb_get_weights: copy the n current FP32 weights to `out` (host).
+ * vjb_set_weights: replace the weights by `w` (host, n values, finite,
+ * >= 0, positive sum), normalised in FP64 and stored FP32, and restart the
+ * round status (training may continue after a DONE status).
+ * Errors: VJB_ESTATE before load; VJB_EINVAL; VJB_ECUDA. */
+int vjb_get_weights(vjb_ctx *ctx, float *out);
+int vjb_set_weights(vjb_ctx *ctx, const float *w);
+
+/* Teacher forcing: run steps 3-4 of a round with a given stump instead of the
+ * searched one: its error on the current weights (FP64), beta, alpha, and the
+ * update.  `feature`, `threshold`, `polarity` as in vjb_stump; *out (host,
+ * may be NULL) receives the completed record.  Statuses as
+ * vjb_train_round.  Errors: VJB_ESTATE; VJB_EINVAL (feature out of range,
+ * polarity not +-1). */
+int vjb_force_stump(vjb_ctx *ctx, int32_t feature, int32_t threshold, int32_t polarity,
+                    vjb_stump *out);
+
+/* Context and last-search diagnostics.  Errors: VJB_EINVAL (out NULL). */
+int vjb_get_info(vjb_ctx *ctx, vjb_info *out);
+
+/* ---- inspection (tests) ----------------------------------------------------
+ * vjb_get_integral: copy the integral images, [n][h+1][w+1] int32 (host).
+ * vjb_feature_values: evaluate features [f0, f0 + nf) on every window into
+ *   out[nf][n] int32 (host).
+ * vjb_sorted_rows: copy rows [f0, f0 + nf) of the sorted table into
+ *   out[nf][n] uint16 (host).  Entry = sample index (bits 0-14) | bit 15 set
+ *   when the value at this position is smaller than the value at the next
+ *   position (always set at the last position).
+ * vjb_screen_errors: copy the F per-feature FP32 errors of the last search
+ *   (host): min over thresholds and polarities of the feature's stump error,
+ *   from FP32 prefix sums with a compensated carry.
+ * Errors: VJB_ESTATE before the data exists; VJB_EINVAL for a range outside
+ * [0, F); VJB_ECUDA. */
+int vjb_get_integral(vjb_ctx *ctx, int32_t *out);
+int vjb_feature_values(vjb_ctx *ctx, int64_t f0, int64_t nf, int32_t *out);
+int vjb_sorted_rows(vjb_ctx *ctx, int64_t f0, int64_t nf, uint16_t *out);
+int vjb_screen_errors(vjb_ctx *ctx, float *out);
+
+/* ---- tuning ------------------------------------------------------------------
+ * Launch shape of the search kernel: consumer warps per CTA (1-16), TMA
+ * stages per warp (2-8) and CTAs per SM (1-4); 0 keeps the current value.
+ * Shapes whose shared memory does not fit are rejected with VJB_EINVAL.
+ * Takes effect from the next round. */
+int vjb_set_search_shape(vjb_ctx *ctx, int32_t warps, int32_t stages, int32_t ctas_per_sm);
+
+/* ---- timing ------------------------------------------------------------------
+ * vjb_set_timing: enable (1) or disable (0) event timing of rounds; enabling
+ * also clears the accumulated figures.  vjb_get_timing: the figures of the
+ * rounds run since (host `out`).  Errors: VJB_EINVAL; VJB_ECUDA. */
+int vjb_set_timing(vjb_ctx *ctx, int32_t enable);
+int vjb_get_timing(vjb_ctx *ctx, vjb_timing *out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VJB_H */

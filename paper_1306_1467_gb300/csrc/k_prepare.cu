@@ -1,0 +1,293 @@
+// One-time preparation kernels: integral images (Sec. 2.1), int32 Haar feature
+// values (Sec. 2.2) and the per-feature stable sample order that the round
+// search scans (the threshold search of Sec. 2.2-2.3 needs the samples of a
+// feature in value order).
+#include <limits.h>
+
+#include "vjb_device.cuh"
+#include "vjb_internal.cuh"
+
+namespace vjb {
+
+// ---- K1: integral images --------------------------------------------------------
+// One thread per window.  Output is point-major, ii_t[(y * (w + 1) + x) * stride + i],
+// so that the feature kernel reads consecutive windows with coalesced loads.
+// ii(x, y) = sum of pixels with x' < x and y' < y (zero first row and column),
+// built row by row: ii(x, y) = ii(x, y - 1) + (sum of row y - 1 up to x - 1).
+__global__ void k_integral(const uint8_t *__restrict__ px, int n, int h, int w,
+                           int32_t *__restrict__ ii_t, int stride) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int W1 = w + 1;
+    const uint8_t *img = px + (size_t)i * h * w;
+    for (int x = 0; x <= w; ++x) ii_t[(size_t)x * stride + i] = 0;
+    for (int y = 1; y <= h; ++y) {
+        ii_t[(size_t)(y * W1) * stride + i] = 0;
+        int32_t row = 0;
+        for (int x = 1; x <= w; ++x) {
+            row += img[(y - 1) * w + (x - 1)];
+            const int32_t up = ii_t[(size_t)((y - 1) * W1 + x) * stride + i];
+            ii_t[(size_t)(y * W1 + x) * stride + i] = up + row;
+        }
+    }
+}
+
+cudaError_t launch_integral(const uint8_t *px, int n, int h, int w, int32_t *ii_t, int ii_stride,
+                            cudaStream_t st) {
+    const int b = 128;
+    k_integral<<<(n + b - 1) / b, b, 0, st>>>(px, n, h, w, ii_t, ii_stride);
+    return cudaGetLastError();
+}
+
+// ---- K2: feature values ------------------------------------------------------------
+// One CTA per feature; threads stride over windows.  out[(f - f0) * n + i].
+__global__ void k_feature_values(const int32_t *__restrict__ ii_t, int stride, int n, int w,
+                                 const DevFeature *__restrict__ feat, int64_t f0,
+                                 int32_t *__restrict__ out) {
+    const DevFeature d = feat[f0 + blockIdx.x];
+    int32_t *o = out + (size_t)blockIdx.x * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        o[i] = haar_value(ii_t, stride, w, d.type, d.x, d.y, d.w, d.h, i);
+}
+
+cudaError_t launch_feature_values(const int32_t *ii_t, int ii_stride, int n, int w,
+                                  const DevFeature *feat, int64_t f0, int64_t nf, int32_t *out,
+                                  cudaStream_t st) {
+    if (nf <= 0) return cudaSuccess;
+    k_feature_values<<<(unsigned)nf, 256, 0, st>>>(ii_t, ii_stride, n, w, feat, f0, out);
+    return cudaGetLastError();
+}
+
+// ---- K3: segmented stable sort ---------------------------------------------------------
+// One 1024-thread CTA per feature row.  Keys are value - min (so they are
+// non-negative), sorted by an LSD radix sort with 8-bit digits over only the
+// bits the row's value span needs.  Each pass ranks digits stably: items are
+// held in registers in a "warp-striped" layout (warp wp, column j, lane l ->
+// position wp*32*IPT + j*32 + l), a warp walks its columns in position order
+// and ranks equal digits inside a column with __match_any_sync, and the
+// per-(digit, warp) counts are scanned digit-major.  Equal keys therefore keep
+// their order, and since items start in sample order, ties end up ordered by
+// sample index.  Output entry = sample index | (value < next value) << 15;
+// positions n .. npad-1 hold the padding entry n (weight 0, no flag).
+constexpr int kSortThreads = 1024;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kRadix = 256;
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan of one int per thread over the CTA; returns the thread's
+// exclusive prefix.  `ws` holds kSortWarps ints.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *ws) {
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    uint32_t inc = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) ws[wp] = inc;
+    __syncthreads();
+    if (wp == 0) {
+        uint32_t t = ws[lane];
+        uint32_t ti = t;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, ti, d);
+            if (lane >= d) ti += y;
+        }
+        ws[lane] = ti - t;
+    }
+    __syncthreads();
+    const uint32_t r = ws[wp] + inc - x;
+    __syncthreads();
+    return r;
+}
+
+template <int IPT>
+__global__ void __launch_bounds__(kSortThreads, 1)
+    k_sort_rows(const int32_t *__restrict__ vals, int n, uint16_t *__restrict__ rows, int npad) {
+    constexpr int NP = kSortThreads * IPT;
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *skey = reinterpret_cast<uint32_t *>(smem);
+    uint32_t *hist = skey + NP;                    // kRadix * kSortWarps
+    uint32_t *ws = hist + kRadix * kSortWarps;     // kSortWarps
+    int32_t *mm = reinterpret_cast<int32_t *>(ws + kSortWarps);  // 2
+    uint16_t *sidx = reinterpret_cast<uint16_t *>(mm + 2);       // NP
+
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int32_t *vr = vals + (size_t)blockIdx.x * n;
+    const int pos0 = wp * 32 * IPT + lane;
+
+    uint32_t key[IPT];
+    uint32_t ipk[(IPT + 1) / 2];  // two 16-bit sample indices per register
+    int32_t lo = INT_MAX, hi = INT_MIN;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int p = pos0 + j * 32;
+        int32_t x = 0;
+        if (p < n) {
+            x = vr[p];
+            lo = min(lo, x);
+            hi = max(hi, x);
+        }
+        key[j] = static_cast<uint32_t>(x);
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    }
+    if (threadIdx.x == 0) { mm[0] = INT_MAX; mm[1] = INT_MIN; }
+    __syncthreads();
+    if (lane == 0) { atomicMin(&mm[0], lo); atomicMax(&mm[1], hi); }
+    __syncthreads();
+    lo = mm[0];
+    hi = mm[1];
+    const uint32_t span = static_cast<uint32_t>(hi) - static_cast<uint32_t>(lo);
+    const int bits = span ? 32 - __clz(span) : 0;
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int p = pos0 + j * 32;
+        // padding items take the all-ones key: they sort after every real item
+        key[j] = (p < n) ? key[j] - static_cast<uint32_t>(lo) : 0xffffffffu;
+        if (j & 1) ipk[j >> 1] |= static_cast<uint32_t>(p) << 16;
+        else ipk[j >> 1] = static_cast<uint32_t>(p) & 0xffffu;
+    }
+
+    const uint32_t lt = lanemask_lt();
+    for (int shift = 0; shift < bits; shift += 8) {
+        for (int k = threadIdx.x; k < kRadix * kSortWarps; k += kSortThreads) hist[k] = 0;
+        __syncthreads();
+        // count digits per (digit, warp)
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const uint32_t d = (key[j] >> shift) & (kRadix - 1);
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (lane == __ffs(peers) - 1) atomicAdd(&hist[d * kSortWarps + wp], __popc(peers));
+        }
+        __syncthreads();
+        // exclusive scan, digit-major then warp: thread t owns 8 consecutive counters
+        {
+            constexpr int PER = kRadix * kSortWarps / kSortThreads;  // 8
+            uint32_t c[PER];
+            uint32_t s = 0;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                c[q] = hist[threadIdx.x * PER + q];
+                s += c[q];
+            }
+            uint32_t off = block_exclusive_scan(s, ws);
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                hist[threadIdx.x * PER + q] = off;
+                off += c[q];
+            }
+        }
+        __syncthreads();
+        // scatter in position order
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const uint32_t d = (key[j] >> shift) & (kRadix - 1);
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const uint32_t base = hist[d * kSortWarps + wp];
+            __syncwarp();
+            if (lane == __ffs(peers) - 1) hist[d * kSortWarps + wp] = base + __popc(peers);
+            __syncwarp();
+            const uint32_t dst = base + __popc(peers & lt);
+            skey[dst] = key[j];
+            sidx[dst] = static_cast<uint16_t>((j & 1) ? (ipk[j >> 1] >> 16) : (ipk[j >> 1] & 0xffffu));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const int p = pos0 + j * 32;
+            key[j] = skey[p];
+            const uint32_t ix = sidx[p];
+            if (j & 1) ipk[j >> 1] = (ipk[j >> 1] & 0xffffu) | (ix << 16);
+            else ipk[j >> 1] = ix;
+        }
+        __syncthreads();
+    }
+    // make the final order visible in shared memory (also when no pass ran)
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int p = pos0 + j * 32;
+        skey[p] = key[j];
+        sidx[p] = static_cast<uint16_t>((j & 1) ? (ipk[j >> 1] >> 16) : (ipk[j >> 1] & 0xffffu));
+    }
+    __syncthreads();
+    uint16_t *out = rows + (size_t)blockIdx.x * npad;
+    for (int p = threadIdx.x; p < npad; p += kSortThreads) {
+        uint16_t e;
+        if (p < n) {
+            const bool step = (p == n - 1) || (skey[p] < skey[p + 1]);
+            e = static_cast<uint16_t>(sidx[p] | (step ? kFlagBit : 0));
+        } else {
+            e = static_cast<uint16_t>(n);
+        }
+        out[p] = e;
+    }
+}
+
+// Validation of a finished table: every entry before position n names a
+// sample below n, every entry from n on is the padding entry n.  Sets
+// kFlagBadTable in `flags` otherwise.  The search kernels rely on this to
+// gather weights without bounds checks.
+__global__ void k_check_rows(const uint4 *__restrict__ rows, int64_t nvec, int n, int npad,
+                             int32_t *flags) {
+    bool bad = false;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvec;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 q = __ldg(rows + k);
+        const int p0 = (int)((k * 8) % npad);
+        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
+            const int p = p0 + j;
+            bad |= (p < n) ? ((e & kIndexMask) >= (uint32_t)n) : (e != (uint32_t)n);
+        }
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagBadTable);
+}
+
+cudaError_t launch_check_rows(const uint16_t *rows, int64_t nfeat, int n, int npad, int32_t *flags,
+                              int grid, cudaStream_t st) {
+    const int64_t nvec = nfeat * (int64_t)npad / 8;
+    k_check_rows<<<grid, 256, 0, st>>>(reinterpret_cast<const uint4 *>(rows), nvec, n, npad, flags);
+    return cudaGetLastError();
+}
+
+template <int IPT>
+static size_t sort_smem() {
+    return (size_t)kSortThreads * IPT * 4 + kRadix * kSortWarps * 4 + kSortWarps * 4 + 8 +
+           (size_t)kSortThreads * IPT * 2;
+}
+
+template <int IPT>
+static cudaError_t launch_sort_ipt(const int32_t *vals, int n, int64_t nf, uint16_t *rows,
+                                   int npad, cudaStream_t st) {
+    const size_t sm = sort_smem<IPT>();
+    cudaError_t e = cudaFuncSetAttribute(k_sort_rows<IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sm);
+    if (e != cudaSuccess) return e;
+    k_sort_rows<IPT><<<(unsigned)nf, kSortThreads, sm, st>>>(vals, n, rows, npad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_rows(const int32_t *vals, int n, int64_t nf, uint16_t *rows, int npad,
+                             cudaStream_t st) {
+    if (nf <= 0) return cudaSuccess;
+    if (n <= kSortThreads * 1) return launch_sort_ipt<1>(vals, n, nf, rows, npad, st);
+    if (n <= kSortThreads * 2) return launch_sort_ipt<2>(vals, n, nf, rows, npad, st);
+    if (n <= kSortThreads * 4) return launch_sort_ipt<4>(vals, n, nf, rows, npad, st);
+    if (n <= kSortThreads * 8) return launch_sort_ipt<8>(vals, n, nf, rows, npad, st);
+    if (n <= kSortThreads * 16) return launch_sort_ipt<16>(vals, n, nf, rows, npad, st);
+    return launch_sort_ipt<32>(vals, n, nf, rows, npad, st);
+}
+
+}  // namespace vjb

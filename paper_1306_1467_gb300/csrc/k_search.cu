@@ -1,0 +1,353 @@
+// Per-round search for the least-error decision stump over every Haar feature
+// (Sec. 2.3 step 2: eps_t = min over f, p, theta of sum_i w_i |h(x_i) - y_i|).
+//
+// For one feature, let the samples be taken in value order (the sorted table)
+// and let D(s) = sum over the first s samples of v_i, v_i = +w_i for a face and
+// -w_i for a non-face.  With T+ and T- the face and non-face weight totals, the
+// stump that puts the first s samples "below" the threshold errs by
+//     T+ - D(s)   for p = +1 (below is a face),
+//     T- + D(s)   for p = -1 (above is a face),
+// and only splits between two different values are thresholds (bit 15 of the
+// entry before the split; s = 0 is always one).  So the feature's least error
+// is min(T+ - max D, T- + min D) over valid splits.
+//
+// Two kernels:
+//  * k_screen (the hot kernel): streams the whole uint16 table once per round
+//    with TMA, gathers v from shared memory, and forms D with FP32 prefix sums:
+//    each lane sums 16 consecutive entries, a warp scan combines the 32 lane
+//    totals of a 512-entry unit, and the running offset of a row is carried in
+//    double-float (compensated) form.  It writes each feature's FP32 error and
+//    each CTA's minimum.
+//  * k_refine: every feature whose screened error is within a margin of the
+//    smallest one is scanned again with double-float (compensated FP32)
+//    arithmetic throughout, giving its best split, polarity and an error to
+//    about 1e-14 relative; the winner among these is picked by the finalize
+//    kernel.
+//
+// Screening error bound (u = 2^-24, sum |v| = T+ + T- = 1 after normalising):
+// a lane's partial sums of 16 terms err by at most 16u times the lane's |v|
+// mass, the 5-level warp scan by 5u times the unit's mass, combining the
+// compensated carry with the unit offset and the lane maximum adds 3u |D|,
+// and forming T+- -/+ D in FP32 adds 2u.  So |screened - exact| <= 26u.  A
+// margin of 64u (twice 32u) keeps every feature that could beat the best one.
+#include <limits.h>
+#include <math.h>
+
+#include "vjb_device.cuh"
+#include "vjb_internal.cuh"
+
+namespace vjb {
+
+__host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+size_t search_smem_bytes(const SearchShape &s, int n) {
+    size_t b = 1024;  // alignment slack for the 1024-byte aligned stage buffers
+    b += (size_t)s.warps * s.stages * kStageBytes;
+    b += align_up((size_t)(n + 1) * 4, 16);
+    b += (size_t)s.warps * s.stages * 8;
+    b += (size_t)s.warps * 4;
+    return b;
+}
+
+// One 512-entry unit of a stage: lane k holds entries 16k .. 16k+15.  The
+// stage was written by TMA with the 128-byte swizzle: within each 1 KiB, the
+// 16-byte chunk c of line r sits at chunk c ^ (r & 7), which makes the two
+// 16-byte reads of the 32 lanes bank-conflict free.
+__device__ __forceinline__ void screen_unit(uint32_t sbase, int unit, int lane, int lines_here,
+                                            uint32_t pad2, const float *__restrict__ sv,
+                                            float &chi, float &clo, float &MX, float &MN) {
+    const uint32_t line = (uint32_t)unit * 8u + ((uint32_t)lane >> 2);
+    const uint32_t sw = ((uint32_t)lane >> 2) & 7u;
+    const uint32_t c0 = ((2u * ((uint32_t)lane & 3u)) ^ sw) << 4;
+    const uint32_t c1 = ((2u * ((uint32_t)lane & 3u) + 1u) ^ sw) << 4;
+    uint4 q0, q1;
+    if (line < (uint32_t)lines_here) {
+        q0 = lds128(sbase + line * kLineBytes + c0);
+        q1 = lds128(sbase + line * kLineBytes + c1);
+    } else {  // lines past the row's end: padding entries (weight 0, no split)
+        q0 = make_uint4(pad2, pad2, pad2, pad2);
+        q1 = q0;
+    }
+    const uint32_t wd[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+    float g[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        g[2 * j] = sv[wd[j] & kIndexMask];
+        g[2 * j + 1] = sv[(wd[j] >> 16) & kIndexMask];
+    }
+    float a = 0.f, mx = -INFINITY, mn = INFINITY;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        a += g[j];
+        const uint32_t fl = (j & 1) ? (wd[j >> 1] & 0x80000000u) : (wd[j >> 1] & 0x8000u);
+        if (fl) {
+            mx = fmaxf(mx, a);
+            mn = fminf(mn, a);
+        }
+    }
+    float x = a;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    float excl = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) excl = 0.f;
+    const float tot = __shfl_sync(0xffffffffu, x, 31);
+    const float base = chi + (clo + excl);
+    MX = fmaxf(MX, base + mx);
+    MN = fminf(MN, base + mn);
+    float s, e;
+    two_sum(chi, tot, s, e);
+    chi = s;
+    clo += e;
+}
+
+__global__ void __launch_bounds__(512, 1)
+    k_screen(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ v, int n,
+             int lines_per_row, int box_lines, int64_t nfeat, int stages, RoundState *rs,
+             float *__restrict__ ferr, float *__restrict__ bmin) {
+    if (rs->status != VJB_OK) return;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(align_up(reinterpret_cast<size_t>(smem_raw), 1024));
+    const int nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *rings = base;
+    float *sv = reinterpret_cast<float *>(rings + (size_t)nw * stages * kStageBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sv + align_up((size_t)(n + 1), 4));
+    float *wbest = reinterpret_cast<float *>(bars + nw * stages);
+
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) sv[i] = (i < n) ? v[i] : 0.f;
+    const uint32_t ring_w = smem_u32(rings + (size_t)warp * stages * kStageBytes);
+    const uint32_t bar_w = smem_u32(bars + warp * stages);
+    if (lane == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(bar_w + 8 * s, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    const int64_t gw = (int64_t)blockIdx.x * nw + warp;
+    const int64_t G = (int64_t)gridDim.x * nw;
+    const int64_t nf_w = gw < nfeat ? (nfeat - 1 - gw) / G + 1 : 0;
+    const int nc = (lines_per_row + box_lines - 1) / box_lines;
+    const int64_t total = nf_w * nc;
+    const uint32_t tx = (uint32_t)box_lines * kLineBytes;
+
+    auto issue = [&](int64_t seq) {
+        const int64_t k = seq / nc;
+        const int c = (int)(seq - k * nc);
+        const int64_t f = gw + k * G;
+        const int stage = (int)(seq % stages);
+        const uint32_t bar = bar_w + 8u * stage;
+        mbar_arrive_expect_tx(bar, tx);
+        tma_load_3d(ring_w + (uint32_t)stage * kStageBytes, &tmap, 0, c * box_lines, (int32_t)f, bar);
+    };
+    if (lane == 0) {
+        const int64_t pro = total < stages ? total : stages;
+        for (int64_t s = 0; s < pro; ++s) issue(s);
+    }
+    __syncwarp();
+
+    const float Tp = (float)rs->t_pos, Tm = (float)rs->t_neg;
+    const uint32_t pad2 = (uint32_t)n | ((uint32_t)n << 16);
+    float best = INFINITY;
+    int64_t seq = 0;
+    bool ok = true;
+    for (int64_t k = 0; k < nf_w && ok; ++k) {
+        const int64_t f = gw + k * G;
+        float chi = 0.f, clo = 0.f, MX = 0.f, MN = 0.f;  // D(0) = 0 is a valid split
+        for (int c = 0; c < nc; ++c) {
+            const int stage = (int)(seq % stages);
+            const uint32_t par = (uint32_t)((seq / stages) & 1);
+            const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * stage, par));
+            if (!got) {
+                ok = false;
+                break;
+            }
+            const int lines_here = min(box_lines, lines_per_row - c * box_lines);
+            const int units = (lines_here + 7) >> 3;
+            const uint32_t sbase = ring_w + (uint32_t)stage * kStageBytes;
+            for (int u = 0; u < units; ++u)
+                screen_unit(sbase, u, lane, lines_here, pad2, sv, chi, clo, MX, MN);
+            __syncwarp();
+            if (lane == 0 && seq + stages < total) {
+                fence_proxy_async_smem();
+                issue(seq + stages);
+            }
+            ++seq;
+        }
+        if (!ok) break;
+        MX = warp_max(MX);
+        MN = warp_min(MN);
+        const float e = fminf(Tp - MX, Tm + MN);
+        if (lane == 0) {
+            ferr[f] = e;
+            best = fminf(best, e);
+        }
+    }
+    if (!ok) {
+        // stop: record the failure and wait (bounded) for this warp's copies in flight
+        if (lane == 0) {
+            atomicOr(&rs->flags, kFlagWaitTimeout);
+            const int64_t issued = (seq + stages < total) ? seq + stages : total;
+            for (int64_t s = seq; s < issued; ++s)
+                mbar_wait_bounded(bar_w + 8u * (uint32_t)(s % stages), (uint32_t)((s / stages) & 1),
+                                  100000000ull);
+        }
+        __syncwarp();
+    }
+    if (lane == 0) wbest[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = INFINITY;
+        for (int w = 0; w < nw; ++w) m = fminf(m, wbest[w]);
+        bmin[blockIdx.x] = m;
+    }
+}
+
+cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, int n, int lines_per_row,
+                          int box_lines, int64_t nfeat, const SearchShape &shape, int grid,
+                          RoundState *rs, float *ferr, float *bmin, cudaStream_t st) {
+    const size_t sm = search_smem_bytes(shape, n);
+    k_screen<<<grid, shape.warps * 32, sm, st>>>(*tmap, v, n, lines_per_row, box_lines, nfeat,
+                                                 shape.stages, rs, ferr, bmin);
+    return cudaGetLastError();
+}
+
+cudaError_t set_screen_smem_limit(int bytes) {
+    return cudaFuncSetAttribute(k_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+int screen_occupancy(const SearchShape &s, int n) {
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_screen, s.warps * 32,
+                                                      search_smem_bytes(s, n)) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+// ---- compensated re-scan of shortlisted features --------------------------------------
+
+__device__ __forceinline__ bool df_eq(DF a, DF b) { return a.hi == b.hi && a.lo == b.lo; }
+
+// Whole warp scans one row in double-float.  Returns the feature's best
+// (error, split, polarity) with ties going to the lower split, then p = +1.
+__device__ Candidate rescan_row(const uint16_t *__restrict__ row, int npad, int n,
+                                const float *__restrict__ v, DF Tp, DF Tm, int lane) {
+    DF carry{0.f, 0.f};
+    DF bmax = lane == 0 ? DF{0.f, 0.f} : DF{-INFINITY, 0.f};
+    DF bmn = lane == 0 ? DF{0.f, 0.f} : DF{INFINITY, 0.f};
+    int smax = lane == 0 ? 0 : INT_MAX, smn = smax;
+    const uint32_t pad2 = (uint32_t)n | ((uint32_t)n << 16);
+    for (int u0 = 0; u0 < npad; u0 += kUnitElems) {
+        const int off = u0 + lane * 16;
+        uint32_t wd[8];
+        if (off < npad) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(row + off);
+            const uint4 a = __ldg(p), b = __ldg(p + 1);
+            wd[0] = a.x; wd[1] = a.y; wd[2] = a.z; wd[3] = a.w;
+            wd[4] = b.x; wd[5] = b.y; wd[6] = b.z; wd[7] = b.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) wd[j] = pad2;
+        }
+        DF a{0.f, 0.f}, lmx{-INFINITY, 0.f}, lmn{INFINITY, 0.f};
+        int lsx = INT_MAX, lsn = INT_MAX;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
+            a = df_add_f(a, __ldg(v + (e & kIndexMask)));
+            if (e & kFlagBit) {
+                const int pos = off + j + 1;
+                if (df_less(lmx, a)) { lmx = a; lsx = pos; }
+                if (df_less(a, lmn)) { lmn = a; lsn = pos; }
+            }
+        }
+        DF x = a;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const DF y = df_shfl_up(x, d);
+            if (lane >= d) x = df_add(y, x);
+        }
+        DF excl = df_shfl_up(x, 1);
+        if (lane == 0) excl = DF{0.f, 0.f};
+        const DF tot = df_shfl(x, 31);
+        const DF offs = df_add(carry, excl);
+        if (lsx != INT_MAX) {
+            const DF c = df_add(offs, lmx);
+            if (df_less(bmax, c)) { bmax = c; smax = lsx; }
+        }
+        if (lsn != INT_MAX) {
+            const DF c = df_add(offs, lmn);
+            if (df_less(c, bmn)) { bmn = c; smn = lsn; }
+        }
+        carry = df_add(carry, tot);
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        const DF om = df_shfl_xor(bmax, d);
+        const int os = __shfl_xor_sync(0xffffffffu, smax, d);
+        if (df_less(bmax, om) || (df_eq(om, bmax) && os < smax)) { bmax = om; smax = os; }
+        const DF on = df_shfl_xor(bmn, d);
+        const int on_s = __shfl_xor_sync(0xffffffffu, smn, d);
+        if (df_less(on, bmn) || (df_eq(on, bmn) && on_s < smn)) { bmn = on; smn = on_s; }
+    }
+    const DF ep = df_add(Tp, df_neg(bmax));
+    const DF em = df_add(Tm, bmn);
+    Candidate c;
+    const bool minus = df_less(em, ep) || (df_eq(em, ep) && smn < smax);
+    c.err_hi = minus ? em.hi : ep.hi;
+    c.err_lo = minus ? em.lo : ep.lo;
+    c.split = minus ? smn : smax;
+    c.polarity = minus ? -1 : 1;
+    c.feature = -1;
+    c.pad = 0;
+    return c;
+}
+
+__global__ void __launch_bounds__(256)
+    k_refine(const uint16_t *__restrict__ rows, int npad, int n, int64_t nfeat,
+             const float *__restrict__ v, RoundState *rs, const float *__restrict__ ferr,
+             const float *__restrict__ bmin, int nbmin, Candidate *__restrict__ cands) {
+    if (rs->status != VJB_OK || rs->forced) return;
+    __shared__ float red[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float m = INFINITY;
+    for (int i = threadIdx.x; i < nbmin; i += blockDim.x) m = fminf(m, bmin[i]);
+    m = warp_min(m);
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    m = INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fminf(m, red[w]);
+    const double tsum = rs->t_pos + rs->t_neg;
+    const float thr = m + kScreenMarginUlps * 5.9604644775390625e-8f * (float)tsum;
+    if (blockIdx.x == 0 && threadIdx.x == 0) rs->screen_min = m;
+    const DF Tp = df_from_double(rs->t_pos), Tm = df_from_double(rs->t_neg);
+    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
+    const int64_t G = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t base = gw * 32; base < nfeat; base += G * 32) {
+        const int64_t f = base + lane;
+        const float e = f < nfeat ? ferr[f] : INFINITY;
+        uint32_t mask = __ballot_sync(0xffffffffu, e <= thr);
+        while (mask) {
+            const int b = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int64_t fc = base + b;
+            Candidate c = rescan_row(rows + (size_t)fc * npad, npad, n, v, Tp, Tm, lane);
+            if (lane == 0) {
+                c.feature = (int32_t)fc;
+                const int slot = atomicAdd(&rs->cand_count, 1);
+                cands[slot] = c;
+            }
+        }
+    }
+}
+
+cudaError_t launch_refine(const uint16_t *rows, int npad, int n, int64_t nfeat, const float *v,
+                          RoundState *rs, const float *ferr, const float *bmin, int nbmin,
+                          Candidate *cands, int grid, cudaStream_t st) {
+    k_refine<<<grid, 256, 0, st>>>(rows, npad, n, nfeat, v, rs, ferr, bmin, nbmin, cands);
+    return cudaGetLastError();
+}
+
+}  // namespace vjb

@@ -1,0 +1,818 @@
+// C ABI of the library (declared in include/vjb.h): context ownership,
+// argument checking, the order of the training steps, and the launch sequence
+// of a boosting round (search -> refine -> finalize), replayed as a CUDA graph
+// by vjb_train_strong.
+#include <stdarg.h>
+#include <stddef.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <vector>
+
+#include "vjb_internal.cuh"
+
+namespace vjb {
+cudaError_t set_screen_smem_limit(int bytes);
+int screen_occupancy(const SearchShape &s, int n);
+}  // namespace vjb
+
+using namespace vjb;
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? VJB_ENOMEM : VJB_ECUDA,       \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));               \
+    } while (0)
+
+template <class T>
+void dfree(T *&p) {
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+constexpr int kStageNone = 0, kStageLoaded = 1, kStageIntegral = 2, kStagePrepared = 3;
+constexpr int kRoundLaunches = 3;  // search, refine, finalize
+
+using EventTriple = std::array<cudaEvent_t, 3>;  // round start, search end, round end
+
+}  // namespace
+
+struct vjb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int max_smem = 0;
+    int stage = kStageNone;
+    int64_t launches = 0;
+
+    int n = 0, h = 0, w = 0;
+    int ii_stride = 0, npad = 0, lines = 0, box_lines = 0;
+    int64_t nfeat = 0;
+
+    uint8_t *d_px = nullptr, *d_y = nullptr;
+    int32_t *d_ii = nullptr;
+    DevFeature *d_feat = nullptr;
+    uint16_t *d_rows = nullptr;
+    float *d_w = nullptr, *d_v = nullptr, *d_wtmp = nullptr;
+    float *d_ferr = nullptr, *d_bmin = nullptr;
+    Candidate *d_cand = nullptr;
+    RoundState *d_rs = nullptr;
+    vjb_stump *d_stumps = nullptr, *d_last = nullptr;
+    int stump_cap = 0;
+    int bmin_cap = 0;
+
+    std::vector<vjb_feature> feats;
+    CUtensorMap tmap;
+    bool tmap_ok = false;
+    SearchShape shape{8, 4, 1};
+    bool shape_set = false;
+    int screen_grid = 0, refine_grid = 0;
+
+    // graph of one round; with timing on it holds three event-record nodes
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_timed = false;
+    cudaGraphNode_t ev_nodes[3] = {nullptr, nullptr, nullptr};
+
+    bool timing = false;
+    std::vector<EventTriple> ev_free, ev_pending;
+    vjb_timing tacc{};
+
+    void drop_graph() {
+        if (gexec) cudaGraphExecDestroy(gexec);
+        if (graph) cudaGraphDestroy(graph);
+        gexec = nullptr;
+        graph = nullptr;
+    }
+    void free_all() {
+        drop_graph();
+        dfree(d_px); dfree(d_y); dfree(d_ii); dfree(d_feat); dfree(d_rows);
+        dfree(d_w); dfree(d_v); dfree(d_wtmp); dfree(d_ferr); dfree(d_bmin); dfree(d_cand);
+        dfree(d_rs); dfree(d_stumps); dfree(d_last);
+        stump_cap = bmin_cap = 0;
+        feats.clear();
+        stage = kStageNone;
+        tmap_ok = false;
+        n = h = w = ii_stride = npad = lines = box_lines = 0;
+        nfeat = 0;
+    }
+    void free_events() {
+        for (auto &t : ev_free) for (auto e : t) cudaEventDestroy(e);
+        for (auto &t : ev_pending) for (auto e : t) cudaEventDestroy(e);
+        ev_free.clear();
+        ev_pending.clear();
+    }
+};
+
+namespace {
+
+int set_dev(vjb_ctx *c) {
+    CK(cudaSetDevice(c->device));
+    return VJB_OK;
+}
+
+int32_t *flags_ptr(vjb_ctx *c) {
+    return reinterpret_cast<int32_t *>(reinterpret_cast<char *>(c->d_rs) + offsetof(RoundState, flags));
+}
+
+// Canonical enumeration (types 3H, 3V, 2H, 2V, 4; then width, height, y, x).
+void enumerate_host(int W, int H, std::vector<vjb_feature> &out) {
+    static const int bw[5] = {3, 1, 2, 1, 2}, bh[5] = {1, 3, 1, 2, 2};
+    out.clear();
+    for (int t = 0; t < 5; ++t)
+        for (int fw = bw[t]; fw <= W; fw += bw[t])
+            for (int fh = bh[t]; fh <= H; fh += bh[t])
+                for (int y = 0; y + fh <= H; ++y)
+                    for (int x = 0; x + fw <= W; ++x)
+                        out.push_back(vjb_feature{(uint8_t)t, (uint8_t)x, (uint8_t)y, (uint8_t)fw, (uint8_t)fh});
+}
+
+int make_tensor_map(vjb_ctx *c) {
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+        if (q != cudaDriverEntryPointSuccess || !fn)
+            return fail(VJB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        encode = reinterpret_cast<EncodeTiledFn>(fn);
+    }
+    // rows of the sorted table as [feature][line][64 entries]
+    cuuint64_t dims[3] = {(cuuint64_t)kLineElems, (cuuint64_t)c->lines, (cuuint64_t)c->nfeat};
+    cuuint64_t strides[2] = {(cuuint64_t)kLineBytes, (cuuint64_t)c->lines * kLineBytes};
+    cuuint32_t box[3] = {(cuuint32_t)kLineElems, (cuuint32_t)c->box_lines, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, c->d_rows, dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(VJB_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    c->tmap_ok = true;
+    return VJB_OK;
+}
+
+bool shape_fits(const vjb_ctx *c, const SearchShape &s) {
+    return search_smem_bytes(s, c->n) <= (size_t)c->max_smem;
+}
+
+int apply_shape(vjb_ctx *c) {
+    c->screen_grid = c->num_sms * c->shape.ctas_per_sm;
+    if (c->screen_grid > c->bmin_cap) {
+        dfree(c->d_bmin);
+        CK(cudaMalloc(&c->d_bmin, sizeof(float) * c->screen_grid));
+        c->bmin_cap = c->screen_grid;
+    }
+    c->refine_grid = c->num_sms * 2;
+    c->shape_set = true;
+    c->drop_graph();
+    return VJB_OK;
+}
+
+int choose_default_shape(vjb_ctx *c) {
+    if (c->shape_set && shape_fits(c, c->shape)) return apply_shape(c);
+    const SearchShape tries[] = {{8, 4, 1}, {8, 3, 1}, {6, 4, 1}, {4, 4, 1}, {4, 3, 1}, {4, 2, 1}, {2, 2, 1}};
+    for (const auto &s : tries)
+        if (shape_fits(c, s)) {
+            c->shape = s;
+            return apply_shape(c);
+        }
+    return fail(VJB_EINVAL, "no search shape fits shared memory for n = %d", c->n);
+}
+
+int ensure_stump_cap(vjb_ctx *c, int need) {
+    if (need <= c->stump_cap) return VJB_OK;
+    int cap = std::max(1024, c->stump_cap);
+    while (cap < need) cap *= 2;
+    vjb_stump *p = nullptr;
+    CK(cudaMalloc(&p, sizeof(vjb_stump) * cap));
+    if (c->d_stumps && c->stump_cap)
+        CK(cudaMemcpyAsync(p, c->d_stumps, sizeof(vjb_stump) * c->stump_cap, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    dfree(c->d_stumps);
+    c->d_stumps = p;
+    c->stump_cap = cap;
+    c->drop_graph();
+    return VJB_OK;
+}
+
+int take_events(vjb_ctx *c, EventTriple &t) {
+    if (c->ev_free.empty()) {
+        for (auto &e : t) CK(cudaEventCreate(&e));
+    } else {
+        t = c->ev_free.back();
+        c->ev_free.pop_back();
+    }
+    return VJB_OK;
+}
+
+// Fold finished event triples into the timing totals (the stream must be idle).
+int collect_timing(vjb_ctx *c) {
+    for (auto &t : c->ev_pending) {
+        float a = 0.f, b = 0.f;
+        CK(cudaEventElapsedTime(&a, t[0], t[1]));
+        CK(cudaEventElapsedTime(&b, t[0], t[2]));
+        if (c->tacc.rounds == 0) {
+            c->tacc.search_ms_min = a;
+            c->tacc.search_ms_max = a;
+        } else {
+            c->tacc.search_ms_min = std::min(c->tacc.search_ms_min, (double)a);
+            c->tacc.search_ms_max = std::max(c->tacc.search_ms_max, (double)a);
+        }
+        c->tacc.rounds += 1;
+        c->tacc.search_ms_total += a;
+        c->tacc.round_ms_total += b;
+        c->ev_free.push_back(t);
+    }
+    c->ev_pending.clear();
+    return VJB_OK;
+}
+
+// The launches of one round (Sec. 2.3 steps 2-4, with step 1 of the next
+// round).  `ev` (may be NULL) brackets the search kernel and the round.
+int enqueue_round(vjb_ctx *c, const EventTriple *ev, unsigned rec_flags) {
+    if (ev) CK(cudaEventRecordWithFlags((*ev)[0], c->stream, rec_flags));
+    CK(launch_screen(&c->tmap, c->d_v, c->n, c->lines, c->box_lines, c->nfeat, c->shape,
+                     c->screen_grid, c->d_rs, c->d_ferr, c->d_bmin, c->stream));
+    if (ev) CK(cudaEventRecordWithFlags((*ev)[1], c->stream, rec_flags));
+    CK(launch_refine(c->d_rows, c->npad, c->n, c->nfeat, c->d_v, c->d_rs, c->d_ferr, c->d_bmin,
+                     c->screen_grid, c->d_cand, c->refine_grid, c->stream));
+    CK(launch_finalize(c->d_rows, c->npad, c->n, c->d_ii, c->ii_stride, c->w, c->d_feat, c->nfeat,
+                       c->d_y, c->d_w, c->d_v, c->d_rs, c->d_cand, c->d_stumps, c->stump_cap,
+                       c->d_last, c->stream));
+    if (ev) CK(cudaEventRecordWithFlags((*ev)[2], c->stream, rec_flags));
+    return VJB_OK;
+}
+
+int ensure_graph(vjb_ctx *c) {
+    if (c->gexec && c->graph_timed == c->timing) return VJB_OK;
+    c->drop_graph();
+    EventTriple cap{};
+    if (c->timing) {
+        int rc = take_events(c, cap);
+        if (rc) return rc;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_round(c, c->timing ? &cap : nullptr, cudaEventRecordExternal);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (c->timing) c->ev_free.push_back(cap);
+    if (rc != VJB_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(VJB_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    if (c->timing) {
+        size_t nn = 0;
+        CK(cudaGraphGetNodes(g, nullptr, &nn));
+        std::vector<cudaGraphNode_t> nodes(nn);
+        CK(cudaGraphGetNodes(g, nodes.data(), &nn));
+        int found = 0;
+        for (auto nd : nodes) {
+            cudaGraphNodeType ty;
+            CK(cudaGraphNodeGetType(nd, &ty));
+            if (ty != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+            for (int k = 0; k < 3; ++k)
+                if (ev == cap[k]) { c->ev_nodes[k] = nd; ++found; }
+        }
+        if (found != 3) {
+            cudaGraphDestroy(g);
+            return fail(VJB_ECUDA, "timed graph has %d of 3 event nodes", found);
+        }
+    }
+    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    if (e != cudaSuccess) {
+        cudaGraphDestroy(g);
+        c->gexec = nullptr;
+        return fail(VJB_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    c->graph = g;
+    c->graph_timed = c->timing;
+    return VJB_OK;
+}
+
+int read_state(vjb_ctx *c, RoundState *rs) {
+    CK(cudaMemcpyAsync(rs, c->d_rs, sizeof(RoundState), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return VJB_OK;
+}
+
+int device_flags_error(const RoundState &rs) {
+    return fail(VJB_EDEVICE, "kernel error flags 0x%x (1 = wait timeout, 2 = no candidate, 4 = bad weights, 8 = bad table)",
+                rs.flags);
+}
+
+int validate_labels(const uint8_t *y, int n) {
+    int l = 0, m = 0;
+    for (int i = 0; i < n; ++i) {
+        if (y[i] > 1) return fail(VJB_EINVAL, "label %d of sample %d is not 0 or 1", (int)y[i], i);
+        if (y[i]) ++l; else ++m;
+    }
+    if (!l || !m) return fail(VJB_EINVAL, "need at least one face and one non-face (got %d, %d)", l, m);
+    return VJB_OK;
+}
+
+int load_common(vjb_ctx *c, const uint8_t *pixels, const uint8_t *labels, int32_t n, int32_t h,
+                int32_t w, bool on_device) {
+    if (!c) return fail(VJB_EINVAL, "context is NULL");
+    if (!pixels || !labels) return fail(VJB_EINVAL, "pixels or labels is NULL");
+    if (n < 2 || n > VJB_MAX_SAMPLES) return fail(VJB_EINVAL, "n = %d outside [2, %d]", n, VJB_MAX_SAMPLES);
+    if (h < 1 || w < 1 || h > VJB_MAX_WINDOW || w > VJB_MAX_WINDOW)
+        return fail(VJB_EINVAL, "window %dx%d outside [1, %d]", w, h, VJB_MAX_WINDOW);
+    int rc = set_dev(c);
+    if (rc) return rc;
+    std::vector<uint8_t> hy((size_t)n);
+    if (on_device) {
+        CK(cudaMemcpy(hy.data(), labels, (size_t)n, cudaMemcpyDeviceToHost));
+    } else {
+        memcpy(hy.data(), labels, (size_t)n);
+    }
+    rc = validate_labels(hy.data(), n);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    const bool same_shape = c->d_px && c->n == n && c->h == h && c->w == w;
+    if (!same_shape) {
+        // a new shape: release everything sized by the old one
+        c->free_all();
+        c->n = n;
+        c->h = h;
+        c->w = w;
+        const size_t npx = (size_t)n * h * w;
+        CK(cudaMalloc(&c->d_px, npx));
+        CK(cudaMalloc(&c->d_y, (size_t)n));
+        CK(cudaMalloc(&c->d_w, sizeof(float) * n));
+        CK(cudaMalloc(&c->d_wtmp, sizeof(float) * n));
+        CK(cudaMalloc(&c->d_v, sizeof(float) * (n + 1)));
+        CK(cudaMalloc(&c->d_rs, sizeof(RoundState)));
+        CK(cudaMalloc(&c->d_last, sizeof(vjb_stump)));
+        rc = ensure_stump_cap(c, 1024);
+        if (rc) return rc;
+    }
+    // same shape: buffers, tables and the round graph are reused; contents are rebuilt
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(c->d_px, pixels, (size_t)n * h * w, kind, c->stream));
+    CK(cudaMemcpyAsync(c->d_y, hy.data(), (size_t)n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->d_rs, 0, sizeof(RoundState), c->stream));
+    CK(cudaMemsetAsync(c->d_last, 0, sizeof(vjb_stump), c->stream));
+    CK(launch_init_weights(c->d_y, n, nullptr, c->d_w, c->d_v, c->d_rs, c->stream));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(c->stream));
+    c->stage = kStageLoaded;
+    return VJB_OK;
+}
+
+int copy_stump_out(vjb_ctx *c, vjb_stump *out) {
+    if (!out) return VJB_OK;
+    CK(cudaMemcpyAsync(out, c->d_last, sizeof(vjb_stump), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return VJB_OK;
+}
+
+// Feature values (K2) and sort (K3) a tile of features at a time, then a check
+// of the finished table.
+int prepare_tables(vjb_ctx *c) {
+    if (c->feats.empty()) {
+        enumerate_host(c->w, c->h, c->feats);
+        c->nfeat = (int64_t)c->feats.size();
+        if (c->nfeat == 0 || c->nfeat > 0x7fffffffLL)
+            return fail(VJB_EINVAL, "window %dx%d has %lld features", c->w, c->h, (long long)c->nfeat);
+        std::vector<DevFeature> df((size_t)c->nfeat);
+        for (size_t k = 0; k < df.size(); ++k) {
+            const vjb_feature &f = c->feats[k];
+            df[k] = DevFeature{f.type, f.x, f.y, f.w, f.h, 0, 0, 0};
+        }
+        CK(cudaMalloc(&c->d_feat, sizeof(DevFeature) * df.size()));
+        CK(cudaMemcpy(c->d_feat, df.data(), sizeof(DevFeature) * df.size(), cudaMemcpyHostToDevice));
+        c->npad = (c->n + kLineElems - 1) / kLineElems * kLineElems;
+        c->lines = c->npad / kLineElems;
+        c->box_lines = std::min(kBoxLinesMax, c->lines);
+    }
+    if (!c->d_rows) CK(cudaMalloc(&c->d_rows, sizeof(uint16_t) * (size_t)c->nfeat * c->npad));
+    const int64_t tile = std::max<int64_t>(1, std::min<int64_t>(c->nfeat, (int64_t(1) << 28) / c->n));
+    int32_t *d_vals = nullptr;
+    CK(cudaMalloc(&d_vals, sizeof(int32_t) * (size_t)tile * c->n));
+    int err = VJB_OK;
+    for (int64_t f0 = 0; f0 < c->nfeat && err == VJB_OK; f0 += tile) {
+        const int64_t nf = std::min(tile, c->nfeat - f0);
+        cudaError_t e = launch_feature_values(c->d_ii, c->ii_stride, c->n, c->w, c->d_feat, f0, nf,
+                                              d_vals, c->stream);
+        if (e == cudaSuccess)
+            e = launch_sort_rows(d_vals, c->n, nf, c->d_rows + (size_t)f0 * c->npad, c->npad, c->stream);
+        if (e != cudaSuccess) err = fail(VJB_ECUDA, "prepare launch failed: %s", cudaGetErrorString(e));
+        c->launches += 2;
+    }
+    cudaError_t se = cudaStreamSynchronize(c->stream);
+    cudaFree(d_vals);
+    if (err) return err;
+    if (se != cudaSuccess) return fail(VJB_ECUDA, "prepare failed: %s", cudaGetErrorString(se));
+    // the search kernels gather through the table without bounds checks: validate it once
+    CK(launch_check_rows(c->d_rows, c->nfeat, c->n, c->npad, flags_ptr(c), c->num_sms * 8, c->stream));
+    c->launches += 1;
+    RoundState rs;
+    int rc = read_state(c, &rs);
+    if (rc) return rc;
+    if (rs.flags) return device_flags_error(rs);
+    if (!c->d_ferr) CK(cudaMalloc(&c->d_ferr, sizeof(float) * c->nfeat));
+    if (!c->d_cand) CK(cudaMalloc(&c->d_cand, sizeof(Candidate) * c->nfeat));
+    if (!c->tmap_ok) {
+        rc = make_tensor_map(c);
+        if (rc) return rc;
+    }
+    if (!c->d_bmin) {
+        rc = choose_default_shape(c);
+        if (rc) return rc;
+    }
+    return VJB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vjb_last_error(void) { return g_err; }
+
+int vjb_create(vjb_ctx **out, int device, void *cuda_stream) {
+    g_err[0] = 0;
+    if (!out) return fail(VJB_EINVAL, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return fail(VJB_EINVAL, "device %d outside [0, %d)", device, ndev);
+    CK(cudaSetDevice(device));
+    vjb_ctx *c = new vjb_ctx();
+    c->device = device;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e == cudaSuccess && prop.major < 10) {
+        delete c;
+        return fail(VJB_ECUDA, "device %d is sm_%d%d; this library is built for sm_103a", device,
+                    prop.major, prop.minor);
+    }
+    if (e == cudaSuccess) {
+        c->num_sms = prop.multiProcessorCount;
+        c->max_smem = (int)prop.sharedMemPerBlockOptin;
+    }
+    if (e == cudaSuccess) e = set_screen_smem_limit(c->max_smem);
+    if (e == cudaSuccess && cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else if (e == cudaSuccess) {
+        e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        c->own_stream = true;
+    }
+    if (e != cudaSuccess) {
+        delete c;
+        return fail(VJB_ECUDA, "context setup failed: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return VJB_OK;
+}
+
+void vjb_destroy(vjb_ctx *c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->free_all();
+    c->free_events();
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int vjb_load_windows(vjb_ctx *c, const uint8_t *pixels, const uint8_t *labels, int32_t n,
+                     int32_t h, int32_t w) {
+    g_err[0] = 0;
+    return load_common(c, pixels, labels, n, h, w, false);
+}
+
+int vjb_load_windows_device(vjb_ctx *c, const uint8_t *pixels, const uint8_t *labels, int32_t n,
+                            int32_t h, int32_t w) {
+    g_err[0] = 0;
+    return load_common(c, pixels, labels, n, h, w, true);
+}
+
+int vjb_build_integral(vjb_ctx *c) {
+    g_err[0] = 0;
+    if (!c) return fail(VJB_EINVAL, "context is NULL");
+    if (c->stage < kStageLoaded) return fail(VJB_ESTATE, "vjb_build_integral before vjb_load_windows");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    if (!c->d_ii) {
+        c->ii_stride = (c->n + 31) / 32 * 32;
+        CK(cudaMalloc(&c->d_ii, sizeof(int32_t) * (size_t)(c->h + 1) * (c->w + 1) * c->ii_stride));
+    }
+    CK(launch_integral(c->d_px, c->n, c->h, c->w, c->d_ii, c->ii_stride, c->stream));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(c->stream));
+    c->stage = kStageIntegral;
+    return VJB_OK;
+}
+
+int vjb_enumerate_haar(vjb_ctx *c, int64_t *count, vjb_feature *out) {
+    g_err[0] = 0;
+    if (!c) return fail(VJB_EINVAL, "context is NULL");
+    if (!count) return fail(VJB_EINVAL, "count is NULL");
+    if (c->stage < kStageIntegral) return fail(VJB_ESTATE, "vjb_enumerate_haar before vjb_build_integral");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    if (c->stage < kStagePrepared) {
+        rc = prepare_tables(c);
+        if (rc) return rc;
+        c->stage = kStagePrepared;
+    }
+    *count = c->nfeat;
+    if (out) memcpy(out, c->feats.data(), sizeof(vjb_feature) * c->feats.size());
+    return VJB_OK;
+}
+
+int vjb_train_round(vjb_ctx *c, vjb_stump *out) {
+    g_err[0] = 0;
+    if (!c) return fail(VJB_EINVAL, "context is NULL");
+    if (c->stage < kStagePrepared) return fail(VJB_ESTATE, "vjb_train_round before vjb_enumerate_haar");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    RoundState rs;
+    rc = read_state(c, &rs);
+    if (rc) return rc;
+    if (rs.status == VJB_OK) {
+        rc = ensure_stump_cap(c, rs.rounds + 1);
+        if (rc) return rc;
+        EventTriple ev{};
+        if (c->timing) {
+            rc = take_events(c, ev);
+            if (rc) return rc;
+        }
+        rc = enqueue_round(c, c->timing ? &ev : nullptr, cudaEventRecordDefault);
+        if (rc) return rc;
+        c->launches += kRoundLaunches;
+        if (c->timing) c->ev_pending.push_back(ev);
+        rc = read_state(c, &rs);
+        if (rc) return rc;
+    }
+    if (rs.flags) return device_flags_error(rs);
+    rc = copy_stump_out(c, out);
+    if (rc) return rc;
+    return rs.status;
+}
+
+int vjb_train_strong(vjb_ctx *c, int32_t T, vjb_stump *out, int32_t *rounds_done) {
+    g_err[0] = 0;
+    if (!c) return fail(VJB_EINVAL, "context is NULL");
+    if (T < 0) return fail(VJB_EINVAL, "T = %d < 0", T);
+    if (c->stage < kStagePrepared) return fail(VJB_ESTATE, "vjb_train_strong before vjb_enumerate_haar");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    RoundState rs;
+    rc = read_state(c, &rs);
+    if (rc) return rc;
+    const int r0 = rs.rounds;
+    if (rs.status == VJB_OK && T > 0) {
+        rc = ensure_stump_cap(c, r0 + T);
+        if (rc) return rc;
+        rc = ensure_graph(c);
+        if (rc) return rc;
+        for (int32_t t = 0; t < T; ++t) {
+            if (c->timing) {
+                EventTriple ev{};
+                rc = take_events(c, ev);
+                if (rc) return rc;
+                for (int k = 0; k < 3; ++k)
+                    CK(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->ev_nodes[k], ev[k]));
+                c->ev_pending.push_back(ev);
+            }
+            CK(cudaGraphLaunch(c->gexec, c->stream));
+            c->launches += kRoundLaunches;
+        }
+        rc = read_state(c, &rs);
+        if (rc) return rc;
+    }
+    if (rs.flags) return device_flags_error(rs);
+    const int kept = rs.rounds - r0;
+    if (out && kept > 0) {
+        CK(cudaMemcpyAsync(out, c->d_stumps + r0, sizeof(vjb_stump) * kept, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (rounds_done) *rounds_done = kept;
+    return rs.status;
+}
+
+int vjb_get_weights(vjb_ctx *c, float *out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(VJB_EINVAL, "NULL argument");
+    if (c->stage < kStageLoaded) return fail(VJB_ESTATE, "no training set loaded");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out, c->d_w, sizeof(float) * c->n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return VJB_OK;
+}
+
+int vjb_set_weights(vjb_ctx *c, const float *wts) {
+    g_err[0] = 0;
+    if (!c || !wts) return fail(VJB_EINVAL, "NULL argument");
+    if (c->stage < kStageLoaded) return fail(VJB_ESTATE, "no training set loaded");
+    double s = 0.0;
+    for (int i = 0; i < c->n; ++i) {
+        if (!std::isfinite(wts[i]) || wts[i] < 0.f) return fail(VJB_EINVAL, "weight %d is negative or not finite", i);
+        s += wts[i];
+    }
+    if (!(s > 0.0)) return fail(VJB_EINVAL, "weights sum to zero");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->d_wtmp, wts, sizeof(float) * c->n, cudaMemcpyHostToDevice, c->stream));
+    CK(launch_init_weights(c->d_y, c->n, c->d_wtmp, c->d_w, c->d_v, c->d_rs, c->stream));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(c->stream));
+    return VJB_OK;
+}
+
+int vjb_force_stump(vjb_ctx *c, int32_t feature, int32_t threshold, int32_t polarity, vjb_stump *out) {
+    g_err[0] = 0;
+    if (!c) return fail(VJB_EINVAL, "context is NULL");
+    if (c->stage < kStagePrepared) return fail(VJB_ESTATE, "vjb_force_stump before vjb_enumerate_haar");
+    if (feature < 0 || feature >= c->nfeat) return fail(VJB_EINVAL, "feature %d out of range", feature);
+    if (polarity != 1 && polarity != -1) return fail(VJB_EINVAL, "polarity %d is not +-1", polarity);
+    int rc = set_dev(c);
+    if (rc) return rc;
+    RoundState rs;
+    rc = read_state(c, &rs);
+    if (rc) return rc;
+    if (rs.status == VJB_OK) {
+        rc = ensure_stump_cap(c, rs.rounds + 1);
+        if (rc) return rc;
+        int32_t f4[4] = {1, feature, threshold, polarity};
+        char *dst = reinterpret_cast<char *>(c->d_rs) + offsetof(RoundState, forced);
+        CK(cudaMemcpyAsync(dst, f4, sizeof f4, cudaMemcpyHostToDevice, c->stream));
+        CK(launch_finalize(c->d_rows, c->npad, c->n, c->d_ii, c->ii_stride, c->w, c->d_feat, c->nfeat,
+                           c->d_y, c->d_w, c->d_v, c->d_rs, c->d_cand, c->d_stumps, c->stump_cap,
+                           c->d_last, c->stream));
+        c->launches += 1;
+        rc = read_state(c, &rs);
+        if (rc) return rc;
+    }
+    if (rs.flags) return device_flags_error(rs);
+    rc = copy_stump_out(c, out);
+    if (rc) return rc;
+    return rs.status;
+}
+
+int vjb_get_info(vjb_ctx *c, vjb_info *out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(VJB_EINVAL, "NULL argument");
+    memset(out, 0, sizeof *out);
+    out->n = c->n;
+    out->h = c->h;
+    out->w = c->w;
+    out->npad = c->npad;
+    out->features = c->nfeat;
+    out->kernel_warps = c->shape.warps;
+    out->kernel_stages = c->shape.stages;
+    out->kernel_ctas = c->screen_grid;
+    out->search_bytes = 2.0 * (double)c->nfeat * (double)c->n;
+    out->launches = c->launches;
+    if (c->stage >= kStageLoaded) {
+        int rc = set_dev(c);
+        if (rc) return rc;
+        RoundState rs;
+        rc = read_state(c, &rs);
+        if (rc) return rc;
+        out->rounds_done = rs.rounds;
+        out->status = rs.status;
+        out->t_pos = rs.t_pos;
+        out->t_neg = rs.t_neg;
+        out->weight_sum = rs.weight_sum;
+        out->screen_min = rs.screen_min;
+        out->candidates = rs.last_cands;
+        out->device_flags = rs.flags;
+    }
+    return VJB_OK;
+}
+
+int vjb_get_integral(vjb_ctx *c, int32_t *out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(VJB_EINVAL, "NULL argument");
+    if (c->stage < kStageIntegral) return fail(VJB_ESTATE, "integral images not built");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    const int P = (c->h + 1) * (c->w + 1);
+    std::vector<int32_t> t((size_t)P * c->ii_stride);
+    CK(cudaMemcpyAsync(t.data(), c->d_ii, sizeof(int32_t) * t.size(), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < c->n; ++i)
+        for (int p = 0; p < P; ++p) out[(size_t)i * P + p] = t[(size_t)p * c->ii_stride + i];
+    return VJB_OK;
+}
+
+int vjb_feature_values(vjb_ctx *c, int64_t f0, int64_t nf, int32_t *out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(VJB_EINVAL, "NULL argument");
+    if (c->stage < kStagePrepared) return fail(VJB_ESTATE, "features not enumerated");
+    if (f0 < 0 || nf < 0 || f0 + nf > c->nfeat) return fail(VJB_EINVAL, "feature range outside [0, F)");
+    if (nf == 0) return VJB_OK;
+    int rc = set_dev(c);
+    if (rc) return rc;
+    int32_t *d = nullptr;
+    CK(cudaMalloc(&d, sizeof(int32_t) * (size_t)nf * c->n));
+    cudaError_t e = launch_feature_values(c->d_ii, c->ii_stride, c->n, c->w, c->d_feat, f0, nf, d, c->stream);
+    c->launches += 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(int32_t) * (size_t)nf * c->n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(VJB_ECUDA, "feature values failed: %s", cudaGetErrorString(e));
+    return VJB_OK;
+}
+
+int vjb_sorted_rows(vjb_ctx *c, int64_t f0, int64_t nf, uint16_t *out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(VJB_EINVAL, "NULL argument");
+    if (c->stage < kStagePrepared) return fail(VJB_ESTATE, "features not enumerated");
+    if (f0 < 0 || nf < 0 || f0 + nf > c->nfeat) return fail(VJB_EINVAL, "feature range outside [0, F)");
+    if (nf == 0) return VJB_OK;
+    int rc = set_dev(c);
+    if (rc) return rc;
+    CK(cudaMemcpy2DAsync(out, sizeof(uint16_t) * c->n, c->d_rows + (size_t)f0 * c->npad,
+                         sizeof(uint16_t) * c->npad, sizeof(uint16_t) * c->n, (size_t)nf,
+                         cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return VJB_OK;
+}
+
+int vjb_screen_errors(vjb_ctx *c, float *out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(VJB_EINVAL, "NULL argument");
+    if (c->stage < kStagePrepared) return fail(VJB_ESTATE, "features not enumerated");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(out, c->d_ferr, sizeof(float) * c->nfeat, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return VJB_OK;
+}
+
+int vjb_set_search_shape(vjb_ctx *c, int32_t warps, int32_t stages, int32_t ctas_per_sm) {
+    g_err[0] = 0;
+    if (!c) return fail(VJB_EINVAL, "context is NULL");
+    SearchShape s = c->shape;
+    if (warps) s.warps = warps;
+    if (stages) s.stages = stages;
+    if (ctas_per_sm) s.ctas_per_sm = ctas_per_sm;
+    if (s.warps < 1 || s.warps > 16 || s.stages < 2 || s.stages > 8 || s.ctas_per_sm < 1 || s.ctas_per_sm > 4)
+        return fail(VJB_EINVAL, "search shape (%d warps, %d stages, %d CTAs/SM) out of range", s.warps, s.stages, s.ctas_per_sm);
+    if (c->n > 0 && !shape_fits(c, s))
+        return fail(VJB_EINVAL, "search shape needs %zu bytes of shared memory (limit %d)", search_smem_bytes(s, c->n), c->max_smem);
+    if (c->n > 0 && screen_occupancy(s, c->n) < s.ctas_per_sm)
+        return fail(VJB_EINVAL, "%d CTAs per SM of this shape do not fit one SM", s.ctas_per_sm);
+    int rc = set_dev(c);
+    if (rc) return rc;
+    c->shape = s;
+    c->shape_set = true;
+    if (c->stage >= kStagePrepared) return apply_shape(c);
+    return VJB_OK;
+}
+
+int vjb_set_timing(vjb_ctx *c, int32_t enable) {
+    g_err[0] = 0;
+    if (!c) return fail(VJB_EINVAL, "context is NULL");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    for (auto &t : c->ev_pending) c->ev_free.push_back(t);
+    c->ev_pending.clear();
+    c->tacc = vjb_timing{};
+    c->timing = enable != 0;
+    return VJB_OK;
+}
+
+int vjb_get_timing(vjb_ctx *c, vjb_timing *out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(VJB_EINVAL, "NULL argument");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->stream));
+    rc = collect_timing(c);
+    if (rc) return rc;
+    *out = c->tacc;
+    return VJB_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,200 @@
+// Device helpers: inline-PTX wrappers for mbarrier / TMA on sm_103a, bounded
+// waits, warp reductions and double-float (compensated FP32) arithmetic.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vjb.h"
+
+namespace vjb {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// ---- mbarrier ------------------------------------------------------------
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of an mbarrier, giving up after about `limit_ns`
+// nanoseconds.  Returns false on timeout.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
+                                                  uint64_t limit_ns = 2000000000ull) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_timer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// ---- TMA ---------------------------------------------------------------------
+
+// 3-D tiled bulk tensor load global -> shared, completion on an mbarrier.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int32_t c0,
+                                            int32_t c1, int32_t c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+// ---- warp reductions ---------------------------------------------------------
+
+__device__ __forceinline__ float warp_max(float x) {
+#pragma unroll
+    for (int d = 16; d; d >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, d));
+    return x;
+}
+
+__device__ __forceinline__ float warp_min(float x) {
+#pragma unroll
+    for (int d = 16; d; d >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, d));
+    return x;
+}
+
+__device__ __forceinline__ double warp_sum_d(double x) {
+#pragma unroll
+    for (int d = 16; d; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    return x;
+}
+
+// ---- double-float (compensated FP32) ------------------------------------------
+// A value is the unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2.
+// TwoSum (Knuth) gives the exact rounding error of one addition.
+
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ DF df_norm(float s, float e) {  // Fast2Sum, |s| >= |e|
+    DF r;
+    r.hi = __fadd_rn(s, e);
+    r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
+    return r;
+}
+
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    return df_norm(s, __fadd_rn(e, a.lo));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return df_norm(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+
+__device__ __forceinline__ bool df_less(DF a, DF b) {
+    return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+__device__ __forceinline__ DF df_from_double(double x) {
+    DF r;
+    r.hi = __double2float_rn(x);
+    r.lo = __double2float_rn(x - (double)r.hi);
+    return r;
+}
+
+__device__ __forceinline__ DF df_shfl_up(DF a, int d) {
+    return DF{__shfl_up_sync(0xffffffffu, a.hi, d), __shfl_up_sync(0xffffffffu, a.lo, d)};
+}
+
+__device__ __forceinline__ DF df_shfl(DF a, int src) {
+    return DF{__shfl_sync(0xffffffffu, a.hi, src), __shfl_sync(0xffffffffu, a.lo, src)};
+}
+
+__device__ __forceinline__ DF df_shfl_xor(DF a, int d) {
+    return DF{__shfl_xor_sync(0xffffffffu, a.hi, d), __shfl_xor_sync(0xffffffffu, a.lo, d)};
+}
+
+// Haar feature value from integral images stored point-major: point (px, py)
+// of sample i is at ii_t[(py * (w + 1) + px) * stride + i].  Rectangle sums use
+// the four corners of Sec. 2.1 (4 + 1 - (2 + 3)); the combination per type is
+// the dark-minus-white reading documented in vjb.h.
+__device__ __forceinline__ int32_t haar_value(const int32_t *__restrict__ ii_t, int stride,
+                                              int w, int type, int x, int y, int fw, int fh,
+                                              int i) {
+    const int W1 = w + 1;
+    auto P = [&](int px, int py) -> int32_t { return __ldg(ii_t + (size_t)(py * W1 + px) * stride + i); };
+    auto R = [&](int rx, int ry, int rw, int rh) -> int32_t {
+        return P(rx + rw, ry + rh) + P(rx, ry) - (P(rx + rw, ry) + P(rx, ry + rh));
+    };
+    switch (type) {
+    case VJB_HAAR_2H: {
+        const int a = fw >> 1;
+        return R(x + a, y, a, fh) - R(x, y, a, fh);
+    }
+    case VJB_HAAR_2V: {
+        const int b = fh >> 1;
+        return R(x, y + b, fw, b) - R(x, y, fw, b);
+    }
+    case VJB_HAAR_3H: {
+        const int a = fw / 3;
+        return R(x + a, y, a, fh) - R(x, y, a, fh) - R(x + 2 * a, y, a, fh);
+    }
+    case VJB_HAAR_3V: {
+        const int b = fh / 3;
+        return R(x, y + b, fw, b) - R(x, y, fw, b) - R(x, y + 2 * b, fw, b);
+    }
+    default: {
+        const int a = fw >> 1, b = fh >> 1;
+        return R(x + a, y, a, b) + R(x, y + b, a, b) - R(x, y, a, b) - R(x + a, y + b, a, b);
+    }
+    }
+}
+
+}  // namespace vjb

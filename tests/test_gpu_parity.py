@@ -1,0 +1,322 @@
+"""Parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Bars (from the method's definition):
+  * integral images, feature values, sorted sample orders and their tie
+    flags: bit-exact;
+  * per-feature FP32 screened errors: within 32 * 2^-24 of the oracle's FP64
+    per-feature minimum (the screening bound is 26 * 2^-24 times the weight
+    total, see k_search.cu);
+  * each round, on the same FP32 weights: the chosen (feature, threshold,
+    polarity) equals the oracle's unless the oracle's two best errors lie
+    within 1e-6 relative, and the weighted error is within 1e-6 relative of
+    the FP64 oracle.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1306_1467_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-6
+SCREEN_TOL = 32 * 2.0 ** -24
+
+
+def _trainer():
+    from paper_1306_1467_gb300 import vjb
+    return vjb.Trainer(0)
+
+
+def _check_rows(rows_gpu, vals, order):
+    n = vals.shape[1]
+    idx = (rows_gpu & 0x7FFF).astype(np.int64)
+    flag = (rows_gpu >> 15).astype(bool)
+    assert np.array_equal(idx, order)
+    sv = np.take_along_axis(vals, order, axis=1)
+    want = np.ones_like(flag)
+    want[:, : n - 1] = sv[:, :-1] < sv[:, 1:]
+    assert np.array_equal(flag, want)
+
+
+def _round_parity(tr, vals, order, y, rounds, vjb):
+    """Same-input parity of `rounds` rounds; returns the list of stumps."""
+    out = []
+    for t in range(rounds):
+        w32 = tr.get_weights()
+        wn = O.normalize(w32.astype(np.float64))
+        best = O.feature_best_sorted(vals, order, y, wn)
+        ref = O.select(best)
+        st, s = tr.train_round()
+        assert st in (vjb.OK, vjb.DONE_PERFECT), st
+        assert abs(s["error"] - ref["err"]) <= REL * ref["err"], (t, s, ref)
+        near_tie = ref["second_err"] - ref["err"] <= REL * ref["err"]
+        got = (s["feature"], s["threshold"], s["polarity"])
+        if not near_tie:
+            assert got == (ref["feature"], ref["threshold"], ref["polarity"]), (t, s, ref)
+        # whatever was chosen is a minimiser of the oracle's definition
+        e_own = O.stump_error(vals[s["feature"]], y, wn, s["threshold"], s["polarity"])
+        assert abs(e_own - ref["err"]) <= REL * ref["err"], (t, e_own, ref)
+        assert abs(s["error"] - e_own) <= 1e-12
+        assert abs(s["beta"] - s["error"] / (1 - s["error"])) <= 1e-15
+        # the update on the same input: w beta^(1-e), renormalised
+        if st == vjb.OK:
+            w_ref = O.normalize(O.update(vals[s["feature"]], y, wn, s["threshold"], s["polarity"], s["beta"]))
+            w_gpu = tr.get_weights().astype(np.float64)
+            assert np.max(np.abs(w_gpu - w_ref) / w_ref) < 2e-7
+        out.append(s)
+    return out
+
+
+@pytest.fixture(scope="module")
+def tiny_gpu(tiny_prepared):
+    P = tiny_prepared
+    tr = _trainer()
+    feats = tr.prepare(P.px, P.y)
+    yield tr, P, feats
+    tr.close()
+
+
+def test_enumeration_matches_oracle(tiny_gpu):
+    tr, P, feats = tiny_gpu
+    assert np.array_equal(feats, P.desc)
+
+
+def test_integral_bit_exact(tiny_gpu):
+    tr, P, _ = tiny_gpu
+    assert np.array_equal(tr.get_integral(), P.ii)
+
+
+def test_feature_values_bit_exact(tiny_gpu):
+    tr, P, _ = tiny_gpu
+    assert np.array_equal(tr.feature_values(0, P.vals.shape[0]), P.vals)
+
+
+def test_sorted_rows_bit_exact(tiny_gpu):
+    tr, P, _ = tiny_gpu
+    _check_rows(tr.sorted_rows(0, P.vals.shape[0]), P.vals, P.order)
+
+
+def test_rounds_same_input_parity(tiny_gpu):
+    from paper_1306_1467_gb300 import vjb
+    tr, P, _ = tiny_gpu
+    w0 = tr.get_weights()
+    l, m = int(P.y.sum()), int((1 - P.y).sum())
+    assert np.allclose(w0[P.y == 1], 1 / (2 * l), rtol=1e-7) and np.allclose(w0[P.y == 0], 1 / (2 * m), rtol=1e-7)
+    _round_parity(tr, P.vals, P.order, P.y, 10, vjb)
+    info = tr.info()
+    assert info["rounds_done"] == 10 and abs(info["weight_sum"] - 1.0) < 1e-6
+
+
+def test_screen_errors_within_bound(tiny_gpu):
+    tr, P, _ = tiny_gpu
+    # errors of the last search were computed on the weights before the last update:
+    # run one more round and compare on its input
+    w = O.normalize(tr.get_weights().astype(np.float64))
+    tr.train_round()
+    ferr = tr.screen_errors().astype(np.float64)
+    best = O.feature_best_sorted(P.vals, P.order, P.y, w)
+    assert np.max(np.abs(ferr - best["err"])) <= SCREEN_TOL
+
+
+def test_train_strong_graph_matches_round_by_round(tiny_prepared):
+    P = tiny_prepared
+    with _trainer() as a, _trainer() as b:
+        a.prepare(P.px, P.y)
+        b.prepare(P.px, P.y)
+        sa = [a.train_round()[1] for _ in range(6)]
+        st, sb = b.train_strong(6)
+        assert st == 0 and len(sb) == 6
+        assert sa == sb
+        assert np.array_equal(a.get_weights(), b.get_weights())
+        st, sc = b.train_strong(3)  # continues the same run
+        assert len(sc) == 3 and b.info()["rounds_done"] == 9
+
+
+def test_trajectory_against_independent_fp64_oracle(tiny_prepared):
+    """An independent FP64 oracle run: same stumps while no near-tie occurs,
+    per-round error drift reported and small."""
+    P = tiny_prepared
+    st, ref, _ = O.train(P.vals, P.order, P.y, O.initial_weights(P.y), 10)
+    with _trainer() as tr:
+        tr.prepare(P.px, P.y)
+        st2, got = tr.train_strong(10)
+    assert len(got) == len(ref) == 10
+    for t, (g, r) in enumerate(zip(got, ref)):
+        if (g["feature"], g["threshold"], g["polarity"]) != (r["feature"], r["threshold"], r["polarity"]):
+            # only allowed where the oracle itself saw a near tie
+            assert r["second_err"] - r["err"] <= 1e-6 * r["err"], (t, g, r)
+            break
+        assert abs(g["error"] - r["err"]) <= 1e-5 * r["err"], (t, g, r)
+
+
+@pytest.mark.parametrize("n_pos,n_neg,h,w", [(300, 477, 9, 7), (5, 3, 4, 4), (1, 1, 3, 3),
+                                             (700, 1400, 12, 16), (1, 2, 1, 2)])
+def test_ragged_shapes(n_pos, n_neg, h, w):
+    """Sample counts that leave ragged TMA boxes, units and lanes; odd windows."""
+    from paper_1306_1467_gb300 import vjb
+    px, y = synth.make_windows(n_pos, n_neg, h, w, seed=77 + n_pos)
+    P = O.Prepared(px, y)
+    with _trainer() as tr:
+        feats = tr.prepare(px, y)
+        assert np.array_equal(feats, P.desc)
+        assert np.array_equal(tr.feature_values(0, feats.shape[0]), P.vals)
+        _check_rows(tr.sorted_rows(0, feats.shape[0]), P.vals, P.order)
+        rounds = 3
+        for t in range(rounds):
+            w32 = tr.get_weights()
+            wn = O.normalize(w32.astype(np.float64))
+            ref = O.select(O.feature_best_sorted(P.vals, P.order, y, wn))
+            st, s = tr.train_round()
+            if st == vjb.DONE_NOGAIN:
+                assert ref["err"] >= 0.5 - 1e-12
+                break
+            assert abs(s["error"] - ref["err"]) <= REL * max(ref["err"], 1e-300)
+            if st == vjb.DONE_PERFECT:
+                assert ref["err"] == 0.0 and math.isinf(s["alpha"])
+                break
+
+
+def test_degenerate_rounds_gpu():
+    from paper_1306_1467_gb300 import vjb
+    px = np.zeros((8, 4, 4), np.uint8)
+    y = np.array([1, 0, 1, 0, 0, 1, 0, 0], np.uint8)
+    px[y == 1, 1, 2] = 200
+    with _trainer() as tr:
+        tr.prepare(px, y)
+        st, stumps = tr.train_strong(5)
+        assert st == vjb.DONE_PERFECT and len(stumps) == 1
+        assert stumps[0]["error"] == 0.0 and math.isinf(stumps[0]["alpha"])
+        st, s = tr.train_round()  # training is over: same status, nothing runs
+        assert st == vjb.DONE_PERFECT and tr.info()["rounds_done"] == 1
+    px2 = np.full((6, 4, 4), 77, np.uint8)
+    y2 = np.array([1, 0, 1, 0, 1, 0], np.uint8)
+    with _trainer() as tr:
+        tr.prepare(px2, y2)
+        st, stumps = tr.train_strong(5)
+        assert st == vjb.DONE_NOGAIN and stumps == []
+
+
+def test_invalid_inputs_rejected():
+    from paper_1306_1467_gb300 import vjb
+    with _trainer() as tr:
+        px = np.zeros((4, 5, 5), np.uint8)
+        with pytest.raises(vjb.VJBError) as e:
+            tr.load_windows(px, np.array([0, 1, 2, 0], np.uint8))
+        assert e.value.code == vjb.EINVAL
+        with pytest.raises(vjb.VJBError) as e:
+            tr.load_windows(px, np.zeros(4, np.uint8))  # no faces
+        assert e.value.code == vjb.EINVAL
+        with pytest.raises(vjb.VJBError) as e:
+            tr.load_windows(np.zeros((1, 5, 5), np.uint8), np.ones(1, np.uint8))
+        assert e.value.code == vjb.EINVAL
+        with pytest.raises(vjb.VJBError) as e:
+            tr.load_windows(np.zeros((vjb.MAX_SAMPLES + 1, 2, 2), np.uint8),
+                            np.arange(vjb.MAX_SAMPLES + 1, dtype=np.int64).astype(np.uint8) & 1)
+        assert e.value.code == vjb.EINVAL
+        with pytest.raises(vjb.VJBError) as e:
+            tr.train_round()  # nothing loaded
+        assert e.value.code == vjb.ESTATE
+        tr.load_windows(px, np.array([0, 1, 1, 0], np.uint8))
+        with pytest.raises(vjb.VJBError) as e:
+            tr.enumerate_haar()  # before build_integral
+        assert e.value.code == vjb.ESTATE
+        tr.build_integral()
+        tr.enumerate_haar()
+        with pytest.raises(vjb.VJBError) as e:
+            tr.force_stump(0, 0, 3)
+        assert e.value.code == vjb.EINVAL
+        with pytest.raises(vjb.VJBError) as e:
+            tr.set_weights(np.array([1, -1, 1, 1], np.float32))
+        assert e.value.code == vjb.EINVAL
+
+
+def test_teacher_forcing_and_weights_roundtrip(tiny_prepared):
+    from paper_1306_1467_gb300 import vjb
+    P = tiny_prepared
+    with _trainer() as tr:
+        tr.prepare(P.px, P.y)
+        rng = np.random.default_rng(11)
+        w = rng.random(P.y.shape[0]).astype(np.float32) + 0.01
+        tr.set_weights(w)
+        got = tr.get_weights().astype(np.float64)
+        assert np.max(np.abs(got - w / w.astype(np.float64).sum())) < 1e-9
+        wn = O.normalize(got)
+        f, th, p = 123, 5, -1
+        st, s = tr.force_stump(f, th, p)
+        assert st == vjb.OK and (s["feature"], s["threshold"], s["polarity"]) == (f, th, p)
+        e = O.stump_error(P.vals[f], P.y, wn, th, p)
+        assert abs(s["error"] - e) <= 1e-12
+        below = int(np.sum(P.vals[f] <= th))
+        assert s["split"] == below
+        w_ref = O.normalize(O.update(P.vals[f], P.y, wn, th, p, s["beta"]))
+        assert np.max(np.abs(tr.get_weights() - w_ref) / w_ref) < 2e-7
+
+
+def test_precision_log_uniform_weights(tiny_prepared):
+    """Weights spread over 1e-12 .. 1: the FP32 search still matches FP64."""
+    from paper_1306_1467_gb300 import vjb
+    P = tiny_prepared
+    with _trainer() as tr:
+        tr.prepare(P.px, P.y)
+        tr.set_weights(synth.log_uniform_weights(P.y.shape[0], seed=5))
+        _round_parity(tr, P.vals, P.order, P.y, 5, vjb)
+
+
+# ---------------------------------------------------------------- full size
+
+def _oracle_best_streaming(px, y, desc, w, block=8192):
+    """Oracle per-feature best over all features, a block of features at a time."""
+    keys = ("err", "split", "polarity", "threshold", "err2")
+    parts = {k: [] for k in keys}
+    ii = O.integral(px)
+    for f0 in range(0, desc.shape[0], block):
+        vals = O.feature_values(px, desc[f0:f0 + block], ii)
+        order = O.sort_rows(vals)
+        b = O.feature_best_sorted(vals, order, y, w)
+        for k in keys:
+            parts[k].append(b[k])
+    return {k: np.concatenate(v) for k, v in parts.items()}
+
+
+@pytest.fixture(scope="module")
+def paper_gpu():
+    px, y, _ = synth.workload("paper_24x24_15k")
+    tr = _trainer()
+    feats = tr.prepare(px, y)
+    yield tr, px, y, feats
+    tr.close()
+
+
+def test_paper_shape_sampled_bit_exact(paper_gpu):
+    """24x24, 15k windows, 162,336 features: sampled features bit-exact."""
+    tr, px, y, feats = paper_gpu
+    assert feats.shape[0] == 162336
+    rng = np.random.default_rng(1307)
+    ii = O.integral(px)
+    pick = rng.choice(px.shape[0], size=64, replace=False)
+    assert np.array_equal(tr.get_integral()[pick], ii[pick])
+    blocks = [0, 27600 - 3, 55200 - 1, 98400, 141600 - 2, 162336 - 64] + list(rng.integers(0, 162336 - 64, 8))
+    for f0 in blocks:
+        f0 = int(f0)
+        vals = O.feature_values(px, feats[f0:f0 + 64], ii)
+        assert np.array_equal(tr.feature_values(f0, 64), vals)
+        _check_rows(tr.sorted_rows(f0, 64), vals, O.sort_rows(vals))
+
+
+def test_paper_shape_full_round_parity(paper_gpu):
+    """One full-size round against the oracle over all 162,336 features."""
+    tr, px, y, feats = paper_gpu
+    wn = O.normalize(tr.get_weights().astype(np.float64))
+    best = _oracle_best_streaming(px, y, feats, wn)
+    ref = O.select(best)
+    st, s = tr.train_round()
+    assert st == 0
+    assert abs(s["error"] - ref["err"]) <= REL * ref["err"], (s, ref)
+    if ref["second_err"] - ref["err"] > REL * ref["err"]:
+        assert (s["feature"], s["threshold"], s["polarity"]) == (ref["feature"], ref["threshold"], ref["polarity"])
+    ferr = tr.screen_errors().astype(np.float64)
+    assert np.max(np.abs(ferr - best["err"])) <= SCREEN_TOL
