@@ -223,6 +223,49 @@ int vjb_set_search_shape(vjb_ctx *ctx, int32_t warps, int32_t stages, int32_t ct
 int vjb_set_timing(vjb_ctx *ctx, int32_t enable);
 int vjb_get_timing(vjb_ctx *ctx, vjb_timing *out);
 
+/* ---- allocation-free search ----------------------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that cannot allocate device memory when they want a search -- a host that
+ * is capturing its own CUDA graph, a real-time loop whose memory is fixed up
+ * front, or a framework whose pool owns all device memory.
+ *
+ * vjb_screen_noalloc runs the per-round FP32 screen (the search kernel of
+ * vjb_train_round, without its compensated re-scan) over a caller-owned
+ * sorted table and allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.  Its scratch (one partial per CTA and a
+ * counter) is a file-scope device array of 8.4 KiB that every GPU loading
+ * the library holds until the process exits; at most 1024 CTAs fit it.
+ *
+ * Arguments (all pointers are device memory on the current device, owned by
+ * the caller):
+ *   rows          [nfeat][npad] uint16 sorted table, 16-byte aligned: entry =
+ *                 sample index (bits 0-14) | bit 15 when the value at this
+ *                 position is below the next one; positions n .. npad-1
+ *                 hold n.  Entries naming a sample above n read as padding.
+ *   v             [n + 1] float: +w_i for a face, -w_i for a non-face,
+ *                 v[n] = 0.
+ *   n, npad       samples (1 .. VJB_MAX_SAMPLES) and row length (a multiple
+ *                 of 64, >= n).
+ *   nfeat         features (rows), 1 .. 2^31 - 1.
+ *   t_pos, t_neg  face and non-face weight totals (finite, >= 0).
+ *   ctas          CTAs to launch, 0 = one per SM; at most 1024.
+ *   feature_err   [nfeat] float out: each feature's least stump error.
+ *   best_err      [1] float out: the smallest of them.
+ *   best_feature  [1] int32 out: its feature (lowest index on ties), or -1
+ *                 if a TMA wait timed out.
+ *   cuda_stream   cudaStream_t to run on (NULL: the legacy default stream).
+ * The call is asynchronous on the stream.  The first call on a device does
+ * that device's set-up (the scratch array's device address, the kernel's
+ * shared-memory limit); make that first call before any stream capture.
+ * Every call shares the one scratch array, so calls that overlap on the GPU
+ * (on two streams, or from two host threads) race; serialise them.
+ * Errors: VJB_EINVAL (a size or pointer outside the limits above, or ctas
+ * above 1024), VJB_ECUDA; vjb_last_error() gives the message. */
+int vjb_screen_noalloc(const uint16_t *rows, const float *v, int32_t n, int32_t npad,
+                       int64_t nfeat, double t_pos, double t_neg, int32_t ctas,
+                       float *feature_err, float *best_err, int32_t *best_feature,
+                       void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

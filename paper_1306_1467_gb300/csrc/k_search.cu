@@ -33,6 +33,10 @@
 #include <limits.h>
 #include <math.h>
 
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
 #include "vjb_device.cuh"
 #include "vjb_internal.cuh"
 
@@ -351,3 +355,296 @@ cudaError_t launch_refine(const uint16_t *rows, int npad, int n, int64_t nfeat, 
 }
 
 }  // namespace vjb
+
+namespace vjb {
+
+// ---- allocation-free variant of the search kernel --------------------------------------
+// Some callers cannot call cudaMalloc at the moment they want a search: a host
+// that is stream-capturing its own CUDA graph, a real-time loop whose memory
+// is fixed up front, or a framework that hands all device memory to its own
+// pool.  vjb_screen_noalloc serves them: the caller passes the sorted table,
+// the signed weights and the outputs, and the only scratch the search needs --
+// one (error, feature) partial per CTA plus a completion counter for the
+// last-CTA reduction -- lives in the file-scope array below.  Every GPU that
+// loads this library holds the array (8.4 KiB) until the process exits, and
+// every call shares it.
+constexpr int kNoAllocMaxCtas = 1024;
+constexpr int kNoAllocWords = 2 * kNoAllocMaxCtas + 64;
+constexpr int kNoAllocDone = 2 * kNoAllocMaxCtas;      // completion counter
+constexpr int kNoAllocFlags = 2 * kNoAllocMaxCtas + 1; // error flags of the call
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+
+// Same unit as screen_unit, with every gathered index clamped to n: the table
+// comes straight from the caller, so an entry above n reads as padding.
+__device__ __forceinline__ void screen_unit_clamped(uint32_t sbase, int unit, int lane,
+                                                    int lines_here, uint32_t n,
+                                                    const float *__restrict__ sv, float &chi,
+                                                    float &clo, float &MX, float &MN) {
+    const uint32_t line = (uint32_t)unit * 8u + ((uint32_t)lane >> 2);
+    const uint32_t sw = ((uint32_t)lane >> 2) & 7u;
+    const uint32_t c0 = ((2u * ((uint32_t)lane & 3u)) ^ sw) << 4;
+    const uint32_t c1 = ((2u * ((uint32_t)lane & 3u) + 1u) ^ sw) << 4;
+    const uint32_t pad2 = n | (n << 16);
+    uint4 q0 = make_uint4(pad2, pad2, pad2, pad2), q1 = q0;
+    if (line < (uint32_t)lines_here) {
+        q0 = lds128(sbase + line * kLineBytes + c0);
+        q1 = lds128(sbase + line * kLineBytes + c1);
+    }
+    const uint32_t wd[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+    float g[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        g[2 * j] = sv[min(wd[j] & kIndexMask, n)];
+        g[2 * j + 1] = sv[min((wd[j] >> 16) & kIndexMask, n)];
+    }
+    float a = 0.f, mx = -INFINITY, mn = INFINITY;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        a += g[j];
+        const uint32_t fl = (j & 1) ? (wd[j >> 1] & 0x80000000u) : (wd[j >> 1] & 0x8000u);
+        if (fl) {
+            mx = fmaxf(mx, a);
+            mn = fminf(mn, a);
+        }
+    }
+    float x = a;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const float y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    float excl = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) excl = 0.f;
+    const float tot = __shfl_sync(0xffffffffu, x, 31);
+    const float base = chi + (clo + excl);
+    MX = fmaxf(MX, base + mx);
+    MN = fminf(MN, base + mn);
+    float s, e;
+    two_sum(chi, tot, s, e);
+    chi = s;
+    clo += e;
+}
+
+__global__ void __launch_bounds__(512, 1)
+    k_screen_noalloc(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ v, int n,
+                     int lines_per_row, int box_lines, int64_t nfeat, int stages, float Tp,
+                     float Tm, float *__restrict__ ferr, float *__restrict__ best_err,
+                     int32_t *__restrict__ best_feature, uint32_t *__restrict__ scratch) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *base = reinterpret_cast<uint8_t *>(align_up(reinterpret_cast<size_t>(smem_raw), 1024));
+    const int nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *rings = base;
+    float *sv = reinterpret_cast<float *>(rings + (size_t)nw * stages * kStageBytes);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sv + align_up((size_t)(n + 1), 4));
+    float *wbest = reinterpret_cast<float *>(bars + nw * stages);
+    __shared__ int32_t wfeat[16];
+    __shared__ bool last_cta;
+
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) sv[i] = (i < n) ? v[i] : 0.f;
+    const uint32_t ring_w = smem_u32(rings + (size_t)warp * stages * kStageBytes);
+    const uint32_t bar_w = smem_u32(bars + warp * stages);
+    if (lane == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(bar_w + 8 * s, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+
+    const int64_t gw = (int64_t)blockIdx.x * nw + warp;
+    const int64_t G = (int64_t)gridDim.x * nw;
+    const int64_t nf_w = gw < nfeat ? (nfeat - 1 - gw) / G + 1 : 0;
+    const int nc = (lines_per_row + box_lines - 1) / box_lines;
+    const int64_t total = nf_w * nc;
+    const uint32_t tx = (uint32_t)box_lines * kLineBytes;
+    auto issue = [&](int64_t seq) {
+        const int64_t k = seq / nc;
+        const int c = (int)(seq - k * nc);
+        const int64_t f = gw + k * G;
+        const int stage = (int)(seq % stages);
+        const uint32_t bar = bar_w + 8u * stage;
+        mbar_arrive_expect_tx(bar, tx);
+        tma_load_3d(ring_w + (uint32_t)stage * kStageBytes, &tmap, 0, c * box_lines, (int32_t)f, bar);
+    };
+    if (lane == 0) {
+        const int64_t pro = total < stages ? total : stages;
+        for (int64_t s = 0; s < pro; ++s) issue(s);
+    }
+    __syncwarp();
+
+    float best = INFINITY;
+    int32_t bestf = 0x7fffffff;
+    int64_t seq = 0;
+    bool ok = true;
+    for (int64_t k = 0; k < nf_w && ok; ++k) {
+        const int64_t f = gw + k * G;
+        float chi = 0.f, clo = 0.f, MX = 0.f, MN = 0.f;
+        for (int c = 0; c < nc; ++c) {
+            const int stage = (int)(seq % stages);
+            const uint32_t par = (uint32_t)((seq / stages) & 1);
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * stage, par))) {
+                ok = false;
+                break;
+            }
+            const int lines_here = min(box_lines, lines_per_row - c * box_lines);
+            const int units = (lines_here + 7) >> 3;
+            const uint32_t sbase = ring_w + (uint32_t)stage * kStageBytes;
+            for (int u = 0; u < units; ++u)
+                screen_unit_clamped(sbase, u, lane, lines_here, (uint32_t)n, sv, chi, clo, MX, MN);
+            __syncwarp();
+            if (lane == 0 && seq + stages < total) {
+                fence_proxy_async_smem();
+                issue(seq + stages);
+            }
+            ++seq;
+        }
+        if (!ok) break;
+        MX = warp_max(MX);
+        MN = warp_min(MN);
+        const float e = fminf(Tp - MX, Tm + MN);
+        if (lane == 0) {
+            ferr[f] = e;
+            if (e < best) { best = e; bestf = (int32_t)f; }
+        }
+    }
+    if (!ok && lane == 0) {
+        atomicOr(&scratch[kNoAllocFlags], (uint32_t)kFlagWaitTimeout);
+        const int64_t issued = (seq + stages < total) ? seq + stages : total;
+        for (int64_t s = seq; s < issued; ++s)
+            mbar_wait_bounded(bar_w + 8u * (uint32_t)(s % stages), (uint32_t)((s / stages) & 1), 100000000ull);
+    }
+    __syncwarp();
+    if (lane == 0) { wbest[warp] = best; wfeat[warp] = bestf; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = INFINITY;
+        int32_t mf = 0x7fffffff;
+        for (int w = 0; w < nw; ++w)
+            if (wbest[w] < m || (wbest[w] == m && wfeat[w] < mf)) { m = wbest[w]; mf = wfeat[w]; }
+        scratch[blockIdx.x] = __float_as_uint(m);
+        scratch[kNoAllocMaxCtas + blockIdx.x] = (uint32_t)mf;
+        __threadfence();
+        last_cta = atomicAdd(&scratch[kNoAllocDone], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last_cta && threadIdx.x == 0) {
+        __threadfence();
+        float m = INFINITY;
+        int32_t mf = -1;
+        for (unsigned b = 0; b < gridDim.x; ++b) {
+            const float e = __uint_as_float(((volatile uint32_t *)scratch)[b]);
+            const int32_t f = (int32_t)((volatile uint32_t *)scratch)[kNoAllocMaxCtas + b];
+            if (e < m || (e == m && f < mf)) { m = e; mf = f; }
+        }
+        const bool failed = ((volatile uint32_t *)scratch)[kNoAllocFlags] != 0u;
+        *best_err = m;
+        *best_feature = failed ? -1 : mf;
+        scratch[kNoAllocDone] = 0u;  // the next call starts from zero
+    }
+}
+
+}  // namespace vjb
+
+namespace {
+
+typedef CUresult (*NoAllocEncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct NoAllocDevice {
+    bool ready = false;
+    uint32_t *scratch = nullptr;  // device address of g_noalloc_scratch on this device
+    int num_sms = 0;
+    int max_smem = 0;             // dynamic shared memory the kernel may use
+};
+constexpr int kNoAllocDevices = 64;
+NoAllocDevice g_noalloc_dev[kNoAllocDevices];
+NoAllocEncodeFn g_noalloc_encode = nullptr;
+std::mutex g_noalloc_mu;
+
+}  // namespace
+
+namespace vjb {
+int report_error(int code, const char *msg);
+}
+
+extern "C" int vjb_screen_noalloc(const uint16_t *rows, const float *v, int32_t n, int32_t npad,
+                                  int64_t nfeat, double t_pos, double t_neg, int32_t ctas,
+                                  float *feature_err, float *best_err, int32_t *best_feature,
+                                  void *cuda_stream) {
+    using namespace vjb;
+    if (!rows || !v || !feature_err || !best_err || !best_feature)
+        return report_error(VJB_EINVAL, "vjb_screen_noalloc: NULL pointer argument");
+    if (n < 1 || n > VJB_MAX_SAMPLES)
+        return report_error(VJB_EINVAL, "vjb_screen_noalloc: n outside [1, VJB_MAX_SAMPLES]");
+    if (npad < n || npad % kLineElems != 0)
+        return report_error(VJB_EINVAL, "vjb_screen_noalloc: npad must be >= n and a multiple of 64");
+    if (nfeat < 1 || nfeat > 0x7fffffffLL)
+        return report_error(VJB_EINVAL, "vjb_screen_noalloc: nfeat outside [1, 2^31 - 1]");
+    if ((reinterpret_cast<uintptr_t>(rows) & 15u) != 0)
+        return report_error(VJB_EINVAL, "vjb_screen_noalloc: rows must be 16-byte aligned");
+    if (!(t_pos >= 0.0) || !(t_neg >= 0.0) || !std::isfinite(t_pos) || !std::isfinite(t_neg))
+        return report_error(VJB_EINVAL, "vjb_screen_noalloc: class totals must be finite and >= 0");
+    if (ctas < 0 || ctas > kNoAllocMaxCtas)
+        return report_error(VJB_EINVAL, "vjb_screen_noalloc: ctas outside [0, 1024] (the scratch array holds 1024 partials)");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocDevices)
+        return report_error(VJB_ECUDA, "vjb_screen_noalloc: no usable current device");
+    NoAllocDevice &D = g_noalloc_dev[dev];
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!D.ready) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+                return report_error(VJB_ECUDA, "vjb_screen_noalloc: cudaGetSymbolAddress of the scratch array failed");
+            int optin = 0;
+            cudaFuncAttributes fa;
+            if (cudaDeviceGetAttribute(&D.num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+                cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+                cudaFuncGetAttributes(&fa, k_screen_noalloc) != cudaSuccess)
+                return report_error(VJB_ECUDA, "vjb_screen_noalloc: device attribute query failed");
+            // the kernel's own static shared memory comes out of the same per-CTA limit
+            D.max_smem = optin - (int)fa.sharedSizeBytes;
+            if (cudaFuncSetAttribute(k_screen_noalloc, cudaFuncAttributeMaxDynamicSharedMemorySize, D.max_smem) != cudaSuccess)
+                return report_error(VJB_ECUDA, "vjb_screen_noalloc: setting the kernel's shared-memory limit failed");
+            if (!g_noalloc_encode) {
+                void *fn = nullptr;
+                cudaDriverEntryPointQueryResult q;
+                if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+                    q != cudaDriverEntryPointSuccess || !fn)
+                    return report_error(VJB_ECUDA, "vjb_screen_noalloc: cuTensorMapEncodeTiled unavailable");
+                g_noalloc_encode = reinterpret_cast<NoAllocEncodeFn>(fn);
+            }
+            D.scratch = static_cast<uint32_t *>(p);
+            D.ready = true;
+        }
+    }
+    const int grid = ctas ? ctas : std::min(D.num_sms, kNoAllocMaxCtas);
+    const SearchShape tries[] = {{8, 4, 1}, {8, 3, 1}, {4, 4, 1}, {4, 2, 1}, {2, 2, 1}};
+    const SearchShape *shape = nullptr;
+    for (const auto &s : tries)
+        if (search_smem_bytes(s, n) <= (size_t)D.max_smem) { shape = &s; break; }
+    if (!shape) return report_error(VJB_EINVAL, "vjb_screen_noalloc: n too large for shared memory");
+    const int lines = npad / kLineElems;
+    const int box_lines = std::min(kBoxLinesMax, lines);
+    CUtensorMap tmap;
+    cuuint64_t dims[3] = {(cuuint64_t)kLineElems, (cuuint64_t)lines, (cuuint64_t)nfeat};
+    cuuint64_t strides[2] = {(cuuint64_t)kLineBytes, (cuuint64_t)lines * kLineBytes};
+    cuuint32_t box[3] = {(cuuint32_t)kLineElems, (cuuint32_t)box_lines, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    if (g_noalloc_encode(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, const_cast<uint16_t *>(rows), dims,
+                         strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return report_error(VJB_EINVAL, "vjb_screen_noalloc: the table cannot be described by a tensor map");
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    // the counter and the flags must start at zero; the partials are all overwritten
+    if (cudaMemsetAsync(D.scratch + kNoAllocDone, 0, 2 * sizeof(uint32_t), st) != cudaSuccess)
+        return report_error(VJB_ECUDA, "vjb_screen_noalloc: clearing the scratch counter failed");
+    k_screen_noalloc<<<grid, shape->warps * 32, search_smem_bytes(*shape, n), st>>>(
+        tmap, v, n, lines, box_lines, nfeat, shape->stages, (float)t_pos, (float)t_neg, feature_err,
+        best_err, best_feature, D.scratch);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return report_error(VJB_ECUDA, cudaGetErrorString(e));
+    return VJB_OK;
+}

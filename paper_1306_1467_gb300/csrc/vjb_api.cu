@@ -450,6 +450,11 @@ int prepare_tables(vjb_ctx *c) {
 
 }  // namespace
 
+namespace vjb {
+// Error reporting for entry points defined in other translation units.
+int report_error(int code, const char *msg) { return fail(code, "%s", msg); }
+}  // namespace vjb
+
 extern "C" {
 
 const char *vjb_last_error(void) { return g_err; }

@@ -91,6 +91,8 @@ SIGNATURES = {
     "vjb_set_search_shape": (C.c_int, [_P, _I32, _I32, _I32]),
     "vjb_set_timing": (C.c_int, [_P, _I32]),
     "vjb_get_timing": (C.c_int, [_P, _P]),
+    "vjb_screen_noalloc": (C.c_int, [_P, _P, _I32, _I32, _I64, C.c_double, C.c_double, _I32,
+                                     _P, _P, _P, _P]),
 }
 
 _lib = None
