@@ -76,6 +76,9 @@ WORKLOADS = {
     "tiny_10x10": dict(n_pos=200, n_neg=400, h=10, w=10, seed=1306, rounds=10),
     "paper_24x24_15k": dict(n_pos=5000, n_neg=10000, h=24, w=24, seed=1307, rounds=200),
     "precision_24x24_15k": dict(n_pos=5000, n_neg=10000, h=24, w=24, seed=1308, rounds=300),
+    # the search kernel's profiling case: the same 15k windows at 16x16, so
+    # the sorted table (32,384 features, 0.97 GB) is larger than L2 but small
+    "search_16x16_15k": dict(n_pos=5000, n_neg=10000, h=16, w=16, seed=1309, rounds=20),
 }
 
 
