@@ -89,9 +89,11 @@ typedef struct {
     int32_t kernel_warps;     /* search kernel: consumer warps per CTA          */
     int32_t kernel_stages;    /* search kernel: TMA stages per warp             */
     int32_t kernel_ctas;      /* search kernel: CTAs in the grid                */
-    int32_t pad;
+    int32_t kernel_unroll;    /* search kernel: 512-entry units a warp works on together */
     double  search_bytes;     /* algorithmic bytes one search reads: 2 * F * N  */
     int64_t launches;         /* kernels this context has launched so far       */
+    int32_t dual_weights;     /* 1: the search gathers from two bank-balanced weight copies */
+    int32_t pad;
 } vjb_info;
 
 /* Per-launch timing of the rounds run since timing was (re)enabled, from CUDA
@@ -210,11 +212,13 @@ int vjb_sorted_rows(vjb_ctx *ctx, int64_t f0, int64_t nf, uint16_t *out);
 int vjb_screen_errors(vjb_ctx *ctx, float *out);
 
 /* ---- tuning ------------------------------------------------------------------
- * Launch shape of the search kernel: consumer warps per CTA (1-16), TMA
- * stages per warp (2-8) and CTAs per SM (1-4); 0 keeps the current value.
- * Shapes whose shared memory does not fit are rejected with VJB_EINVAL.
- * Takes effect from the next round. */
-int vjb_set_search_shape(vjb_ctx *ctx, int32_t warps, int32_t stages, int32_t ctas_per_sm);
+ * Launch shape of the search kernel: consumer warps per CTA (1-16; at most 8
+ * with unroll 4), TMA stages per warp (2-8), CTAs per SM (1-4) and the number
+ * of 512-entry units a warp works on together (1, 2 or 4); 0 keeps the
+ * current value.  Shapes whose shared memory does not fit are rejected with
+ * VJB_EINVAL.  Takes effect from the next round. */
+int vjb_set_search_shape(vjb_ctx *ctx, int32_t warps, int32_t stages, int32_t ctas_per_sm,
+                         int32_t unroll);
 
 /* ---- timing ------------------------------------------------------------------
  * vjb_set_timing: enable (1) or disable (0) event timing of rounds; enabling

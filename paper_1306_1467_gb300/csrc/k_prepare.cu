@@ -72,6 +72,11 @@ cudaError_t launch_feature_values(const int32_t *ii_t, int ii_stride, int n, int
 constexpr int kSortThreads = 1024;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadix = 256;
+// Gather groups of a row with two weight copies (n <= 16352): at most 32
+// units of 512 entries x 16 slots.  Their masks sit after the histogram and
+// the per-thread bank loads (32 bytes each) reuse the histogram space.
+constexpr int kMaxGroups = 512;
+static_assert(kSortThreads * 32 / 4 <= kRadix * kSortWarps, "histogram space too small for bank loads");
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
@@ -109,12 +114,13 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *w
 
 template <int IPT>
 __global__ void __launch_bounds__(kSortThreads, 1)
-    k_sort_rows(const int32_t *__restrict__ vals, int n, uint16_t *__restrict__ rows, int npad) {
+    k_sort_rows(const int32_t *__restrict__ vals, WeightLayout L, uint16_t *__restrict__ rows, int npad) {
     constexpr int NP = kSortThreads * IPT;
+    const int n = L.n;
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *skey = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *hist = skey + NP;                    // kRadix * kSortWarps
-    uint32_t *ws = hist + kRadix * kSortWarps;     // kSortWarps
+    uint32_t *hist = skey + NP;                    // kRadix * kSortWarps (+ kMaxGroups)
+    uint32_t *ws = hist + kRadix * kSortWarps + (IPT <= 16 ? kMaxGroups : 0);  // kSortWarps
     int32_t *mm = reinterpret_cast<int32_t *>(ws + kSortWarps);  // 2
     uint16_t *sidx = reinterpret_cast<uint16_t *>(mm + 2);       // NP
 
@@ -221,6 +227,76 @@ __global__ void __launch_bounds__(kSortThreads, 1)
     }
     __syncthreads();
     uint16_t *out = rows + (size_t)blockIdx.x * npad;
+    if constexpr (IPT <= 16) {
+        if (L.dual) {
+            // With two weight copies, choose per entry which copy the search
+            // gathers from.  One gather instruction of the search kernel reads,
+            // for a 512-entry unit u and a slot j in 0..15, the 32 entries at
+            // u*512 + 16k + j (k = 0..31).  For each such group, greedily put each
+            // entry in the less loaded of its two banks (copy A: i mod 32, copy
+            // B: rot(i) mod 32), then move entries out of the fullest bank while
+            // that lowers the maximum.
+            uint32_t *gchoice = hist + kRadix * kSortWarps;  // one mask per group
+            uint8_t *ld = reinterpret_cast<uint8_t *>(hist) + (size_t)threadIdx.x * 32;
+            const int ngroups = (npad + kUnitElems - 1) / kUnitElems * 16;
+            for (int g = threadIdx.x; g < ngroups; g += kSortThreads) {
+#pragma unroll
+                for (int b = 0; b < 32; ++b) ld[b] = 0;
+                const int u = g >> 4, j = g & 15;
+                uint32_t mask = 0;
+                bool pad_seen = false;
+                for (int k = 0; k < 32; ++k) {
+                    const int p = u * kUnitElems + 16 * k + j;
+                    if (p >= npad) break;
+                    if (p >= n) {
+                        if (!pad_seen) ld[n & 31]++;  // the padding word, read as a broadcast
+                        pad_seen = true;
+                        continue;
+                    }
+                    const int i = sidx[p];
+                    const int ba = i & 31, bb = rot_b(i) & 31;
+                    if (ld[bb] < ld[ba]) { ld[bb]++; mask |= 1u << k; }
+                    else ld[ba]++;
+                }
+                for (int it = 0; it < 32; ++it) {
+                    int m = 0;
+                    for (int b = 0; b < 32; ++b) m = max(m, (int)ld[b]);
+                    bool moved = false;
+                    for (int k = 0; k < 32 && !moved; ++k) {
+                        const int p = u * kUnitElems + 16 * k + j;
+                        if (p >= n || p >= npad) break;
+                        const int i = sidx[p];
+                        const int ba = i & 31, bb = rot_b(i) & 31;
+                        const bool onb = (mask >> k) & 1u;
+                        const int cur = onb ? bb : ba, oth = onb ? ba : bb;
+                        if (ld[cur] == m && ld[oth] + 1 < m) {
+                            ld[cur]--;
+                            ld[oth]++;
+                            mask ^= 1u << k;
+                            moved = true;
+                        }
+                    }
+                    if (!moved) break;
+                }
+                gchoice[g] = mask;
+            }
+            __syncthreads();
+            for (int p = threadIdx.x; p < npad; p += kSortThreads) {
+                uint16_t e;
+                if (p < n) {
+                    const bool step = (p == n - 1) || (skey[p] < skey[p + 1]);
+                    int word = sidx[p];
+                    const int g = (p / kUnitElems) * 16 + (p & 15), k = (p % kUnitElems) >> 4;
+                    if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
+                    e = static_cast<uint16_t>(word | (step ? kFlagBit : 0));
+                } else {
+                    e = static_cast<uint16_t>(n);
+                }
+                out[p] = e;
+            }
+            return;
+        }
+    }
     for (int p = threadIdx.x; p < npad; p += kSortThreads) {
         uint16_t e;
         if (p < n) {
@@ -234,12 +310,13 @@ __global__ void __launch_bounds__(kSortThreads, 1)
 }
 
 // Validation of a finished table: every entry before position n names a
-// sample below n, every entry from n on is the padding entry n.  Sets
-// kFlagBadTable in `flags` otherwise.  The search kernels rely on this to
-// gather weights without bounds checks.
-__global__ void k_check_rows(const uint4 *__restrict__ rows, int64_t nvec, int n, int npad,
+// sample below n through a word of the weight array, every entry from n on is
+// the padding word n.  Sets kFlagBadTable in `flags` otherwise.  The search
+// kernels rely on this to gather weights without bounds checks.
+__global__ void k_check_rows(const uint4 *__restrict__ rows, int64_t nvec, WeightLayout L, int npad,
                              int32_t *flags) {
     bool bad = false;
+    const int n = L.n;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvec;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint4 q = __ldg(rows + k);
@@ -249,45 +326,56 @@ __global__ void k_check_rows(const uint4 *__restrict__ rows, int64_t nvec, int n
         for (int j = 0; j < 8; ++j) {
             const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
             const int p = p0 + j;
-            bad |= (p < n) ? ((e & kIndexMask) >= (uint32_t)n) : (e != (uint32_t)n);
+            const int word = (int)(e & kIndexMask);
+            if (p < n) {
+                const bool ok = word < n || (L.dual && word >= L.off_b && word < L.words &&
+                                             unrot_b(word - L.off_b) < n);
+                bad |= !ok;
+            } else {
+                bad |= e != (uint32_t)n;
+            }
         }
     }
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagBadTable);
 }
 
-cudaError_t launch_check_rows(const uint16_t *rows, int64_t nfeat, int n, int npad, int32_t *flags,
-                              int grid, cudaStream_t st) {
+cudaError_t launch_check_rows(const uint16_t *rows, int64_t nfeat, const WeightLayout &L, int npad,
+                              int32_t *flags, int grid, cudaStream_t st) {
     const int64_t nvec = nfeat * (int64_t)npad / 8;
-    k_check_rows<<<grid, 256, 0, st>>>(reinterpret_cast<const uint4 *>(rows), nvec, n, npad, flags);
+    k_check_rows<<<grid, 256, 0, st>>>(reinterpret_cast<const uint4 *>(rows), nvec, L, npad, flags);
     return cudaGetLastError();
 }
 
 template <int IPT>
 static size_t sort_smem() {
-    return (size_t)kSortThreads * IPT * 4 + kRadix * kSortWarps * 4 + kSortWarps * 4 + 8 +
+    const size_t hist_words = kRadix * kSortWarps + (IPT <= 16 ? kMaxGroups : 0);
+    return (size_t)kSortThreads * IPT * 4 + hist_words * 4 + kSortWarps * 4 + 8 +
            (size_t)kSortThreads * IPT * 2;
 }
 
 template <int IPT>
-static cudaError_t launch_sort_ipt(const int32_t *vals, int n, int64_t nf, uint16_t *rows,
-                                   int npad, cudaStream_t st) {
+static cudaError_t launch_sort_ipt(const int32_t *vals, const WeightLayout &L, int64_t nf,
+                                   uint16_t *rows, int npad, cudaStream_t st) {
     const size_t sm = sort_smem<IPT>();
     cudaError_t e = cudaFuncSetAttribute(k_sort_rows<IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
-    k_sort_rows<IPT><<<(unsigned)nf, kSortThreads, sm, st>>>(vals, n, rows, npad);
+    k_sort_rows<IPT><<<(unsigned)nf, kSortThreads, sm, st>>>(vals, L, rows, npad);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort_rows(const int32_t *vals, int n, int64_t nf, uint16_t *rows, int npad,
-                             cudaStream_t st) {
+cudaError_t launch_sort_rows(const int32_t *vals, const WeightLayout &L, int64_t nf, uint16_t *rows,
+                             int npad, cudaStream_t st) {
     if (nf <= 0) return cudaSuccess;
-    if (n <= kSortThreads * 1) return launch_sort_ipt<1>(vals, n, nf, rows, npad, st);
-    if (n <= kSortThreads * 2) return launch_sort_ipt<2>(vals, n, nf, rows, npad, st);
-    if (n <= kSortThreads * 4) return launch_sort_ipt<4>(vals, n, nf, rows, npad, st);
-    if (n <= kSortThreads * 8) return launch_sort_ipt<8>(vals, n, nf, rows, npad, st);
-    if (n <= kSortThreads * 16) return launch_sort_ipt<16>(vals, n, nf, rows, npad, st);
-    return launch_sort_ipt<32>(vals, n, nf, rows, npad, st);
+    const int n = L.n;
+    // two weight copies need the bank-choice space, which the 32-item variant lacks
+    if (L.dual && n > kSortThreads * 16) return cudaErrorInvalidValue;
+    if (n <= kSortThreads * 1) return launch_sort_ipt<1>(vals, L, nf, rows, npad, st);
+    if (n <= kSortThreads * 2) return launch_sort_ipt<2>(vals, L, nf, rows, npad, st);
+    if (n <= kSortThreads * 4) return launch_sort_ipt<4>(vals, L, nf, rows, npad, st);
+    if (n <= kSortThreads * 8) return launch_sort_ipt<8>(vals, L, nf, rows, npad, st);
+    if (n <= kSortThreads * 16) return launch_sort_ipt<16>(vals, L, nf, rows, npad, st);
+    return launch_sort_ipt<32>(vals, L, nf, rows, npad, st);
 }
 
 }  // namespace vjb

@@ -11,18 +11,19 @@
 // entry before the split; s = 0 is always one).  So the feature's least error
 // is min(T+ - max D, T- + min D) over valid splits.
 //
-// Two kernels:
+// Three kernels per search:
 //  * k_screen (the hot kernel): streams the whole uint16 table once per round
 //    with TMA, gathers v from shared memory, and forms D with FP32 prefix sums:
 //    each lane sums 16 consecutive entries, a warp scan combines the 32 lane
 //    totals of a 512-entry unit, and the running offset of a row is carried in
 //    double-float (compensated) form.  It writes each feature's FP32 error and
 //    each CTA's minimum.
-//  * k_refine: every feature whose screened error is within a margin of the
-//    smallest one is scanned again with double-float (compensated FP32)
-//    arithmetic throughout, giving its best split, polarity and an error to
-//    about 1e-14 relative; the winner among these is picked by the finalize
-//    kernel.
+//  * k_shortlist: lists every feature whose screened error is within a margin
+//    of the smallest one.
+//  * k_rescan: one CTA per listed feature scans its row again in double-float
+//    (compensated FP32) arithmetic throughout, giving the feature's best split,
+//    polarity and an error to about 1e-14 relative; the last CTA to finish
+//    picks the round's stump: lowest error, then feature, split, +1 before -1.
 //
 // Screening error bound (u = 2^-24, sum |v| = T+ + T- = 1 after normalising):
 // a lane's partial sums of 16 terms err by at most 16u times the lane's |v|
@@ -44,86 +45,132 @@ namespace vjb {
 
 __host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-size_t search_smem_bytes(const SearchShape &s, int n) {
-    size_t b = 1024;  // alignment slack for the 1024-byte aligned stage buffers
+// Dynamic shared memory of k_screen: the weight array at the base, then (from
+// the next 1 KiB boundary) the per-warp TMA rings, their mbarriers and the
+// per-warp minima.
+size_t search_smem_bytes(const SearchShape &s, int words) {
+    size_t b = align_up((size_t)words * 4, 16);
+    b += 1024;  // alignment of the rings to 1 KiB
     b += (size_t)s.warps * s.stages * kStageBytes;
-    b += align_up((size_t)(n + 1) * 4, 16);
     b += (size_t)s.warps * s.stages * 8;
-    b += (size_t)s.warps * 4;
+    b += (size_t)s.warps * 4 + 16;
     return b;
 }
 
-// One 512-entry unit of a stage: lane k holds entries 16k .. 16k+15.  The
-// stage was written by TMA with the 128-byte swizzle: within each 1 KiB, the
-// 16-byte chunk c of line r sits at chunk c ^ (r & 7), which makes the two
-// 16-byte reads of the 32 lanes bank-conflict free.
-__device__ __forceinline__ void screen_unit(uint32_t sbase, int unit, int lane, int lines_here,
-                                            uint32_t pad2, const float *__restrict__ sv,
-                                            float &chi, float &clo, float &MX, float &MN) {
-    const uint32_t line = (uint32_t)unit * 8u + ((uint32_t)lane >> 2);
+WeightLayout make_layout(int n, bool allow_dual) {
+    WeightLayout L;
+    L.n = n;
+    const int off_b = (int)align_up((size_t)n + 1, 32);
+    const int words_dual = off_b + (int)align_up((size_t)n, 32);
+    // table entries hold 15-bit word offsets
+    L.dual = (allow_dual && words_dual <= 32768) ? 1 : 0;
+    L.off_b = L.dual ? off_b : 0;
+    L.words = L.dual ? words_dual : (int)align_up((size_t)n + 1, 4);
+    return L;
+}
+
+// Predicated running max/min: update only where `flag` is set (a valid split).
+__device__ __forceinline__ void minmax_if(uint32_t flag, float a, float &mx, float &mn) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %2, 0;\n\t"
+        "@p max.f32 %0, %0, %3;\n\t"
+        "@p min.f32 %1, %1, %3;\n\t}"
+        : "+f"(mx), "+f"(mn)
+        : "r"(flag), "f"(a));
+}
+
+// U consecutive 512-entry units of a stage, worked on together for
+// instruction-level parallelism.  Lane k holds entries 16k .. 16k+15 of each
+// unit.  The stage was written by TMA with the 128-byte swizzle: within each
+// 1 KiB, the 16-byte chunk c of line r sits at chunk c ^ (r & 7), which makes
+// the two 16-byte reads of the 32 lanes bank-conflict free.  Lines at or past
+// `lines_here` read as padding (weight 0, no split).  The arithmetic of each
+// unit, and the order in which units enter the carry, are those of one unit
+// at a time.
+template <int U>
+__device__ __forceinline__ void screen_units(uint32_t sbase, int u0, int lane, int lines_here,
+                                             uint32_t pad2, const float *sv, float &chi,
+                                             float &clo, float &MX, float &MN) {
     const uint32_t sw = ((uint32_t)lane >> 2) & 7u;
     const uint32_t c0 = ((2u * ((uint32_t)lane & 3u)) ^ sw) << 4;
     const uint32_t c1 = ((2u * ((uint32_t)lane & 3u) + 1u) ^ sw) << 4;
-    uint4 q0, q1;
-    if (line < (uint32_t)lines_here) {
-        q0 = lds128(sbase + line * kLineBytes + c0);
-        q1 = lds128(sbase + line * kLineBytes + c1);
-    } else {  // lines past the row's end: padding entries (weight 0, no split)
-        q0 = make_uint4(pad2, pad2, pad2, pad2);
-        q1 = q0;
-    }
-    const uint32_t wd[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-    float g[16];
+    uint32_t wd[U][8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        g[2 * j] = sv[wd[j] & kIndexMask];
-        g[2 * j + 1] = sv[(wd[j] >> 16) & kIndexMask];
-    }
-    float a = 0.f, mx = -INFINITY, mn = INFINITY;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-        a += g[j];
-        const uint32_t fl = (j & 1) ? (wd[j >> 1] & 0x80000000u) : (wd[j >> 1] & 0x8000u);
-        if (fl) {
-            mx = fmaxf(mx, a);
-            mn = fminf(mn, a);
+    for (int u = 0; u < U; ++u) {
+        const uint32_t line = (uint32_t)(u0 + u) * 8u + ((uint32_t)lane >> 2);
+        uint4 q0 = make_uint4(pad2, pad2, pad2, pad2), q1 = q0;
+        if (line < (uint32_t)lines_here) {
+            q0 = lds128(sbase + line * kLineBytes + c0);
+            q1 = lds128(sbase + line * kLineBytes + c1);
         }
+        wd[u][0] = q0.x; wd[u][1] = q0.y; wd[u][2] = q0.z; wd[u][3] = q0.w;
+        wd[u][4] = q1.x; wd[u][5] = q1.y; wd[u][6] = q1.z; wd[u][7] = q1.w;
     }
-    float x = a;
+    float g[U][16];
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const float y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            g[u][2 * j] = sv[wd[u][j] & kIndexMask];
+            g[u][2 * j + 1] = sv[(wd[u][j] >> 16) & kIndexMask];
+        }
+    float a[U], mx[U], mn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        a[u] = 0.f;
+        mx[u] = -INFINITY;
+        mn[u] = INFINITY;
     }
-    float excl = __shfl_up_sync(0xffffffffu, x, 1);
-    if (lane == 0) excl = 0.f;
-    const float tot = __shfl_sync(0xffffffffu, x, 31);
-    const float base = chi + (clo + excl);
-    MX = fmaxf(MX, base + mx);
-    MN = fminf(MN, base + mn);
-    float s, e;
-    two_sum(chi, tot, s, e);
-    chi = s;
-    clo += e;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a[u] += g[u][j];
+            const uint32_t fl = (j & 1) ? (wd[u][j >> 1] & 0x80000000u) : (wd[u][j >> 1] & 0x8000u);
+            minmax_if(fl, a[u], mx[u], mn[u]);
+        }
+    float x[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) x[u] = a[u];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const float y = __shfl_up_sync(0xffffffffu, x[u], d);
+            if (lane >= d) x[u] += y;
+        }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        float excl = __shfl_up_sync(0xffffffffu, x[u], 1);
+        if (lane == 0) excl = 0.f;
+        const float tot = __shfl_sync(0xffffffffu, x[u], 31);
+        const float base = chi + (clo + excl);
+        MX = fmaxf(MX, base + mx[u]);
+        MN = fminf(MN, base + mn[u]);
+        float s, e;
+        two_sum(chi, tot, s, e);
+        chi = s;
+        clo += e;
+    }
 }
 
-__global__ void __launch_bounds__(512, 1)
-    k_screen(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ v, int n,
-             int lines_per_row, int box_lines, int64_t nfeat, int stages, RoundState *rs,
-             float *__restrict__ ferr, float *__restrict__ bmin) {
+template <int U>
+__global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
+    k_screen(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ v, int words,
+             int pad_word, int lines_per_row, int box_lines, int64_t nfeat, int stages,
+             RoundState *rs, float *__restrict__ ferr, float *__restrict__ bmin) {
     if (rs->status != VJB_OK) return;
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t *base = reinterpret_cast<uint8_t *>(align_up(reinterpret_cast<size_t>(smem_raw), 1024));
+    extern __shared__ __align__(16) float sv[];  // weights at the base of dynamic shared memory
     const int nw = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint8_t *rings = base;
-    float *sv = reinterpret_cast<float *>(rings + (size_t)nw * stages * kStageBytes);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sv + align_up((size_t)(n + 1), 4));
-    float *wbest = reinterpret_cast<float *>(bars + nw * stages);
+    const uint32_t sv32 = smem_u32(sv);
+    const uint32_t ring0 = (uint32_t)align_up(sv32 + (uint32_t)words * 4u, 1024);
+    const uint32_t bars0 = ring0 + (uint32_t)(nw * stages * kStageBytes);
+    float *wbest = reinterpret_cast<float *>(reinterpret_cast<char *>(sv) + (bars0 + nw * stages * 8 - sv32));
 
-    for (int i = threadIdx.x; i <= n; i += blockDim.x) sv[i] = (i < n) ? v[i] : 0.f;
-    const uint32_t ring_w = smem_u32(rings + (size_t)warp * stages * kStageBytes);
-    const uint32_t bar_w = smem_u32(bars + warp * stages);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) sv[i] = v[i];
+    const uint32_t ring_w = ring0 + (uint32_t)(warp * stages * kStageBytes);
+    const uint32_t bar_w = bars0 + (uint32_t)(warp * stages * 8);
     if (lane == 0) {
         for (int s = 0; s < stages; ++s) mbar_init(bar_w + 8 * s, 1);
         fence_barrier_init();
@@ -153,7 +200,7 @@ __global__ void __launch_bounds__(512, 1)
     __syncwarp();
 
     const float Tp = (float)rs->t_pos, Tm = (float)rs->t_neg;
-    const uint32_t pad2 = (uint32_t)n | ((uint32_t)n << 16);
+    const uint32_t pad2 = (uint32_t)pad_word | ((uint32_t)pad_word << 16);
     float best = INFINITY;
     int64_t seq = 0;
     bool ok = true;
@@ -163,16 +210,21 @@ __global__ void __launch_bounds__(512, 1)
         for (int c = 0; c < nc; ++c) {
             const int stage = (int)(seq % stages);
             const uint32_t par = (uint32_t)((seq / stages) & 1);
-            const bool got = __all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * stage, par));
-            if (!got) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * stage, par))) {
                 ok = false;
                 break;
             }
             const int lines_here = min(box_lines, lines_per_row - c * box_lines);
-            const int units = (lines_here + 7) >> 3;
             const uint32_t sbase = ring_w + (uint32_t)stage * kStageBytes;
-            for (int u = 0; u < units; ++u)
-                screen_unit(sbase, u, lane, lines_here, pad2, sv, chi, clo, MX, MN);
+            if (lines_here == kBoxLinesMax) {
+#pragma unroll
+                for (int u0 = 0; u0 < kBoxLinesMax / 8; u0 += U)
+                    screen_units<U>(sbase, u0, lane, kBoxLinesMax, pad2, sv, chi, clo, MX, MN);
+            } else {
+                const int units = (lines_here + 7) >> 3;
+                for (int u0 = 0; u0 < units; u0 += U)
+                    screen_units<U>(sbase, u0, lane, lines_here, pad2, sv, chi, clo, MX, MN);
+            }
             __syncwarp();
             if (lane == 0 && seq + stages < total) {
                 fence_proxy_async_smem();
@@ -209,42 +261,123 @@ __global__ void __launch_bounds__(512, 1)
     }
 }
 
-cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, int n, int lines_per_row,
-                          int box_lines, int64_t nfeat, const SearchShape &shape, int grid,
-                          RoundState *rs, float *ferr, float *bmin, cudaStream_t st) {
-    const size_t sm = search_smem_bytes(shape, n);
-    k_screen<<<grid, shape.warps * 32, sm, st>>>(*tmap, v, n, lines_per_row, box_lines, nfeat,
-                                                 shape.stages, rs, ferr, bmin);
+cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, const WeightLayout &L,
+                          int lines_per_row, int box_lines, int64_t nfeat, const SearchShape &shape,
+                          int grid, RoundState *rs, float *ferr, float *bmin, cudaStream_t st) {
+    const size_t sm = search_smem_bytes(shape, L.words);
+    const int threads = shape.warps * 32;
+    switch (shape.unroll) {
+    case 1:
+        k_screen<1><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines, nfeat,
+                                               shape.stages, rs, ferr, bmin);
+        break;
+    case 4:
+        k_screen<4><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines, nfeat,
+                                               shape.stages, rs, ferr, bmin);
+        break;
+    default:
+        k_screen<2><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines, nfeat,
+                                               shape.stages, rs, ferr, bmin);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t set_screen_smem_limit(int bytes) {
-    return cudaFuncSetAttribute(k_screen, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_screen<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_screen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_screen<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
 }
 
-int screen_occupancy(const SearchShape &s, int n) {
+int screen_max_warps(int unroll) { return unroll >= 4 ? 8 : 16; }
+
+int screen_occupancy(const SearchShape &s, int words) {
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_screen, s.warps * 32,
-                                                      search_smem_bytes(s, n)) != cudaSuccess)
-        return 0;
-    return blocks;
+    cudaError_t e;
+    const size_t sm = search_smem_bytes(s, words);
+    if (s.unroll == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_screen<1>, s.warps * 32, sm);
+    else if (s.unroll == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_screen<4>, s.warps * 32, sm);
+    else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_screen<2>, s.warps * 32, sm);
+    return e == cudaSuccess ? blocks : 0;
+}
+
+// ---- shortlist ------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256)
+    k_shortlist(int64_t nfeat, RoundState *rs, const float *__restrict__ ferr,
+                const float *__restrict__ bmin, int nbmin, int32_t *__restrict__ cand_ids) {
+    if (rs->status != VJB_OK || rs->forced) return;
+    __shared__ float red[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float m = INFINITY;
+    for (int i = threadIdx.x; i < nbmin; i += blockDim.x) m = fminf(m, bmin[i]);
+    m = warp_min(m);
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    m = INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fminf(m, red[w]);
+    const double tsum = rs->t_pos + rs->t_neg;
+    const float thr = m + kScreenMarginUlps * 5.9604644775390625e-8f * (float)tsum;
+    if (blockIdx.x == 0 && threadIdx.x == 0) rs->screen_min = m;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + warp * 32; base < nfeat; base += stride) {
+        const int64_t f = base + lane;
+        const bool take = f < nfeat && ferr[f] <= thr;
+        const uint32_t mask = __ballot_sync(0xffffffffu, take);
+        if (!mask) continue;
+        int slot0 = 0;
+        if (lane == 0) slot0 = atomicAdd(&rs->cand_count, __popc(mask));
+        slot0 = __shfl_sync(0xffffffffu, slot0, 0);
+        if (take) cand_ids[slot0 + __popc(mask & ((1u << lane) - 1u))] = (int32_t)f;
+    }
+}
+
+cudaError_t launch_shortlist(int64_t nfeat, RoundState *rs, const float *ferr, const float *bmin,
+                             int nbmin, int32_t *cand_ids, int grid, cudaStream_t st) {
+    k_shortlist<<<grid, 256, 0, st>>>(nfeat, rs, ferr, bmin, nbmin, cand_ids);
+    return cudaGetLastError();
 }
 
 // ---- compensated re-scan of shortlisted features --------------------------------------
 
 __device__ __forceinline__ bool df_eq(DF a, DF b) { return a.hi == b.hi && a.lo == b.lo; }
 
-// Whole warp scans one row in double-float.  Returns the feature's best
-// (error, split, polarity) with ties going to the lower split, then p = +1.
-__device__ Candidate rescan_row(const uint16_t *__restrict__ row, int npad, int n,
-                                const float *__restrict__ v, DF Tp, DF Tm, int lane) {
-    DF carry{0.f, 0.f};
-    DF bmax = lane == 0 ? DF{0.f, 0.f} : DF{-INFINITY, 0.f};
-    DF bmn = lane == 0 ? DF{0.f, 0.f} : DF{INFINITY, 0.f};
-    int smax = lane == 0 ? 0 : INT_MAX, smn = smax;
-    const uint32_t pad2 = (uint32_t)n | ((uint32_t)n << 16);
-    for (int u0 = 0; u0 < npad; u0 += kUnitElems) {
-        const int off = u0 + lane * 16;
+// Lexicographic candidate order: error (double-float), feature, split, +1 first.
+__device__ __forceinline__ bool cand_less(const Candidate &a, const Candidate &b) {
+    if (a.err_hi != b.err_hi) return a.err_hi < b.err_hi;
+    if (a.err_lo != b.err_lo) return a.err_lo < b.err_lo;
+    if (a.feature != b.feature) return a.feature < b.feature;
+    if (a.split != b.split) return a.split < b.split;
+    return a.polarity > b.polarity;
+}
+
+__device__ __forceinline__ Candidate cand_shfl_xor(const Candidate &c, int d) {
+    Candidate o;
+    o.err_hi = __shfl_xor_sync(0xffffffffu, c.err_hi, d);
+    o.err_lo = __shfl_xor_sync(0xffffffffu, c.err_lo, d);
+    o.feature = __shfl_xor_sync(0xffffffffu, c.feature, d);
+    o.split = __shfl_xor_sync(0xffffffffu, c.split, d);
+    o.polarity = __shfl_xor_sync(0xffffffffu, c.polarity, d);
+    o.pad = 0;
+    return o;
+}
+
+constexpr int kRescanWarps = 8;
+
+struct SliceResult {
+    DF total, mx, mn;
+    int smx, smn;
+};
+
+// One warp scans units [ua, ub) of a row in double-float; returns (lane 0) the
+// slice total and its largest / smallest prefix at a valid split, relative to
+// the slice start, with the lowest position on ties (INT_MAX if none).
+__device__ SliceResult rescan_slice(const uint16_t *__restrict__ row, int npad, int ua, int ub,
+                                    const float *__restrict__ v, uint32_t pad2, int lane) {
+    DF carry{0.f, 0.f}, bmax{-INFINITY, 0.f}, bmn{INFINITY, 0.f};
+    int smax = INT_MAX, smn = INT_MAX;
+    for (int u = ua; u < ub; ++u) {
+        const int off = u * kUnitElems + lane * 16;
         uint32_t wd[8];
         if (off < npad) {
             const uint4 *p = reinterpret_cast<const uint4 *>(row + off);
@@ -255,13 +388,19 @@ __device__ Candidate rescan_row(const uint16_t *__restrict__ row, int npad, int 
 #pragma unroll
             for (int j = 0; j < 8; ++j) wd[j] = pad2;
         }
+        float g[16];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            g[2 * j] = __ldg(v + (wd[j] & kIndexMask));
+            g[2 * j + 1] = __ldg(v + ((wd[j] >> 16) & kIndexMask));
+        }
         DF a{0.f, 0.f}, lmx{-INFINITY, 0.f}, lmn{INFINITY, 0.f};
         int lsx = INT_MAX, lsn = INT_MAX;
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
-            a = df_add_f(a, __ldg(v + (e & kIndexMask)));
-            if (e & kFlagBit) {
+            a = df_add_f(a, g[j]);
+            const uint32_t fl = (j & 1) ? (wd[j >> 1] & 0x80000000u) : (wd[j >> 1] & 0x8000u);
+            if (fl) {
                 const int pos = off + j + 1;
                 if (df_less(lmx, a)) { lmx = a; lsx = pos; }
                 if (df_less(a, lmn)) { lmn = a; lsn = pos; }
@@ -296,61 +435,106 @@ __device__ Candidate rescan_row(const uint16_t *__restrict__ row, int npad, int 
         const int on_s = __shfl_xor_sync(0xffffffffu, smn, d);
         if (df_less(on, bmn) || (df_eq(on, bmn) && on_s < smn)) { bmn = on; smn = on_s; }
     }
-    const DF ep = df_add(Tp, df_neg(bmax));
-    const DF em = df_add(Tm, bmn);
-    Candidate c;
-    const bool minus = df_less(em, ep) || (df_eq(em, ep) && smn < smax);
-    c.err_hi = minus ? em.hi : ep.hi;
-    c.err_lo = minus ? em.lo : ep.lo;
-    c.split = minus ? smn : smax;
-    c.polarity = minus ? -1 : 1;
-    c.feature = -1;
-    c.pad = 0;
-    return c;
+    SliceResult r;
+    r.total = carry;
+    r.mx = bmax;
+    r.mn = bmn;
+    r.smx = smax;
+    r.smn = smn;
+    return r;
 }
 
-__global__ void __launch_bounds__(256)
-    k_refine(const uint16_t *__restrict__ rows, int npad, int n, int64_t nfeat,
-             const float *__restrict__ v, RoundState *rs, const float *__restrict__ ferr,
-             const float *__restrict__ bmin, int nbmin, Candidate *__restrict__ cands) {
+__global__ void __launch_bounds__(kRescanWarps * 32)
+    k_rescan(const uint16_t *__restrict__ rows, int npad, const float *__restrict__ v, int pad_word,
+             RoundState *rs, const int32_t *__restrict__ cand_ids, Candidate *__restrict__ cands) {
     if (rs->status != VJB_OK || rs->forced) return;
-    __shared__ float red[8];
+    __shared__ SliceResult sres[kRescanWarps];
+    __shared__ Candidate wc[kRescanWarps];
+    __shared__ bool last_cta;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float m = INFINITY;
-    for (int i = threadIdx.x; i < nbmin; i += blockDim.x) m = fminf(m, bmin[i]);
-    m = warp_min(m);
-    if (lane == 0) red[warp] = m;
-    __syncthreads();
-    m = INFINITY;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fminf(m, red[w]);
-    const double tsum = rs->t_pos + rs->t_neg;
-    const float thr = m + kScreenMarginUlps * 5.9604644775390625e-8f * (float)tsum;
-    if (blockIdx.x == 0 && threadIdx.x == 0) rs->screen_min = m;
+    const int cnt = rs->cand_count;
+    const int units = (npad + kUnitElems - 1) / kUnitElems;
+    const uint32_t pad2 = (uint32_t)pad_word | ((uint32_t)pad_word << 16);
     const DF Tp = df_from_double(rs->t_pos), Tm = df_from_double(rs->t_neg);
-    const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
-    const int64_t G = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t base = gw * 32; base < nfeat; base += G * 32) {
-        const int64_t f = base + lane;
-        const float e = f < nfeat ? ferr[f] : INFINITY;
-        uint32_t mask = __ballot_sync(0xffffffffu, e <= thr);
-        while (mask) {
-            const int b = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int64_t fc = base + b;
-            Candidate c = rescan_row(rows + (size_t)fc * npad, npad, n, v, Tp, Tm, lane);
-            if (lane == 0) {
-                c.feature = (int32_t)fc;
-                const int slot = atomicAdd(&rs->cand_count, 1);
-                cands[slot] = c;
+    for (int c = blockIdx.x; c < cnt; c += gridDim.x) {
+        const int32_t f = cand_ids[c];
+        const uint16_t *row = rows + (size_t)f * npad;
+        const int ua = units * warp / kRescanWarps, ub = units * (warp + 1) / kRescanWarps;
+        const SliceResult r = rescan_slice(row, npad, ua, ub, v, pad2, lane);
+        if (lane == 0) sres[warp] = r;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            DF offs{0.f, 0.f}, bmax{0.f, 0.f}, bmn{0.f, 0.f};  // split 0: D = 0
+            int smax = 0, smn = 0;
+            for (int w = 0; w < kRescanWarps; ++w) {
+                const SliceResult &q = sres[w];
+                if (q.smx != INT_MAX) {
+                    const DF cc = df_add(offs, q.mx);
+                    if (df_less(bmax, cc)) { bmax = cc; smax = q.smx; }
+                }
+                if (q.smn != INT_MAX) {
+                    const DF cc = df_add(offs, q.mn);
+                    if (df_less(cc, bmn)) { bmn = cc; smn = q.smn; }
+                }
+                offs = df_add(offs, q.total);
             }
+            const DF ep = df_add(Tp, df_neg(bmax));
+            const DF em = df_add(Tm, bmn);
+            const bool minus = df_less(em, ep) || (df_eq(em, ep) && smn < smax);
+            Candidate cd;
+            cd.err_hi = minus ? em.hi : ep.hi;
+            cd.err_lo = minus ? em.lo : ep.lo;
+            cd.split = minus ? smn : smax;
+            cd.polarity = minus ? -1 : 1;
+            cd.feature = f;
+            cd.pad = 0;
+            cands[c] = cd;
         }
+        __syncthreads();
+    }
+    // the last CTA to finish picks the round's stump
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_cta = atomicAdd(&rs->done_rescan, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last_cta) return;
+    __threadfence();
+    Candidate b;
+    b.err_hi = INFINITY; b.err_lo = 0.f; b.feature = INT_MAX; b.split = INT_MAX; b.polarity = 1; b.pad = 0;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        Candidate c;
+        const volatile Candidate *vc = cands + k;
+        c.err_hi = vc->err_hi; c.err_lo = vc->err_lo; c.feature = vc->feature;
+        c.split = vc->split; c.polarity = vc->polarity; c.pad = 0;
+        if (cand_less(c, b)) b = c;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        const Candidate o = cand_shfl_xor(b, d);
+        if (cand_less(o, b)) b = o;
+    }
+    if (lane == 0) wc[warp] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kRescanWarps; ++w)
+            if (cand_less(wc[w], b)) b = wc[w];
+        if (cnt == 0 || b.feature == INT_MAX) {
+            rs->flags |= kFlagNoCandidate;
+            rs->status = VJB_EDEVICE;
+        } else {
+            rs->win_feature = b.feature;
+            rs->win_split = b.split;
+            rs->win_polarity = b.polarity;
+        }
+        rs->done_rescan = 0u;
     }
 }
 
-cudaError_t launch_refine(const uint16_t *rows, int npad, int n, int64_t nfeat, const float *v,
-                          RoundState *rs, const float *ferr, const float *bmin, int nbmin,
-                          Candidate *cands, int grid, cudaStream_t st) {
-    k_refine<<<grid, 256, 0, st>>>(rows, npad, n, nfeat, v, rs, ferr, bmin, nbmin, cands);
+cudaError_t launch_rescan(const uint16_t *rows, int npad, const float *v, const WeightLayout &L,
+                          RoundState *rs, const int32_t *cand_ids, Candidate *cands, int grid,
+                          cudaStream_t st) {
+    k_rescan<<<grid, kRescanWarps * 32, 0, st>>>(rows, npad, v, L.n, rs, cand_ids, cands);
     return cudaGetLastError();
 }
 
@@ -373,6 +557,17 @@ constexpr int kNoAllocWords = 2 * kNoAllocMaxCtas + 64;
 constexpr int kNoAllocDone = 2 * kNoAllocMaxCtas;      // completion counter
 constexpr int kNoAllocFlags = 2 * kNoAllocMaxCtas + 1; // error flags of the call
 static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+
+// Dynamic shared memory of k_screen_noalloc: the TMA rings first (1 KiB
+// aligned), then the n + 1 weights, the mbarriers and the per-warp minima.
+static size_t noalloc_smem_bytes(const SearchShape &s, int n) {
+    size_t b = 1024;
+    b += (size_t)s.warps * s.stages * kStageBytes;
+    b += align_up((size_t)(n + 1) * 4, 16);
+    b += (size_t)s.warps * s.stages * 8;
+    b += (size_t)s.warps * 4;
+    return b;
+}
 
 // Same unit as screen_unit, with every gathered index clamped to n: the table
 // comes straight from the caller, so an entry above n reads as padding.
@@ -624,7 +819,7 @@ extern "C" int vjb_screen_noalloc(const uint16_t *rows, const float *v, int32_t 
     const SearchShape tries[] = {{8, 4, 1}, {8, 3, 1}, {4, 4, 1}, {4, 2, 1}, {2, 2, 1}};
     const SearchShape *shape = nullptr;
     for (const auto &s : tries)
-        if (search_smem_bytes(s, n) <= (size_t)D.max_smem) { shape = &s; break; }
+        if (noalloc_smem_bytes(s, n) <= (size_t)D.max_smem) { shape = &s; break; }
     if (!shape) return report_error(VJB_EINVAL, "vjb_screen_noalloc: n too large for shared memory");
     const int lines = npad / kLineElems;
     const int box_lines = std::min(kBoxLinesMax, lines);
@@ -641,7 +836,7 @@ extern "C" int vjb_screen_noalloc(const uint16_t *rows, const float *v, int32_t 
     // the counter and the flags must start at zero; the partials are all overwritten
     if (cudaMemsetAsync(D.scratch + kNoAllocDone, 0, 2 * sizeof(uint32_t), st) != cudaSuccess)
         return report_error(VJB_ECUDA, "vjb_screen_noalloc: clearing the scratch counter failed");
-    k_screen_noalloc<<<grid, shape->warps * 32, search_smem_bytes(*shape, n), st>>>(
+    k_screen_noalloc<<<grid, shape->warps * 32, noalloc_smem_bytes(*shape, n), st>>>(
         tmap, v, n, lines, box_lines, nfeat, shape->stages, (float)t_pos, (float)t_neg, feature_err,
         best_err, best_feature, D.scratch);
     const cudaError_t e = cudaGetLastError();

@@ -16,7 +16,8 @@
 
 namespace vjb {
 cudaError_t set_screen_smem_limit(int bytes);
-int screen_occupancy(const SearchShape &s, int n);
+int screen_occupancy(const SearchShape &s, int words);
+int screen_max_warps(int unroll);
 }  // namespace vjb
 
 using namespace vjb;
@@ -53,7 +54,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 constexpr int kStageNone = 0, kStageLoaded = 1, kStageIntegral = 2, kStagePrepared = 3;
-constexpr int kRoundLaunches = 3;  // search, refine, finalize
+constexpr int kRoundLaunches = 5;  // screen, shortlist, rescan, update a, update b
 
 using EventTriple = std::array<cudaEvent_t, 3>;  // round start, search end, round end
 
@@ -71,6 +72,7 @@ struct vjb_ctx {
     int n = 0, h = 0, w = 0;
     int ii_stride = 0, npad = 0, lines = 0, box_lines = 0;
     int64_t nfeat = 0;
+    WeightLayout lay{};
 
     uint8_t *d_px = nullptr, *d_y = nullptr;
     int32_t *d_ii = nullptr;
@@ -79,6 +81,9 @@ struct vjb_ctx {
     float *d_w = nullptr, *d_v = nullptr, *d_wtmp = nullptr;
     float *d_ferr = nullptr, *d_bmin = nullptr;
     Candidate *d_cand = nullptr;
+    int32_t *d_cand_ids = nullptr;
+    uint8_t *d_miss = nullptr;
+    double *d_partials = nullptr;
     RoundState *d_rs = nullptr;
     vjb_stump *d_stumps = nullptr, *d_last = nullptr;
     int stump_cap = 0;
@@ -87,9 +92,9 @@ struct vjb_ctx {
     std::vector<vjb_feature> feats;
     CUtensorMap tmap;
     bool tmap_ok = false;
-    SearchShape shape{8, 4, 1};
+    SearchShape shape{8, 4, 1, 2};
     bool shape_set = false;
-    int screen_grid = 0, refine_grid = 0;
+    int screen_grid = 0, shortlist_grid = 0, rescan_grid = 0;
 
     // graph of one round; with timing on it holds three event-record nodes
     cudaGraph_t graph = nullptr;
@@ -111,6 +116,7 @@ struct vjb_ctx {
         drop_graph();
         dfree(d_px); dfree(d_y); dfree(d_ii); dfree(d_feat); dfree(d_rows);
         dfree(d_w); dfree(d_v); dfree(d_wtmp); dfree(d_ferr); dfree(d_bmin); dfree(d_cand);
+        dfree(d_cand_ids); dfree(d_miss); dfree(d_partials);
         dfree(d_rs); dfree(d_stumps); dfree(d_last);
         stump_cap = bmin_cap = 0;
         feats.clear();
@@ -118,6 +124,7 @@ struct vjb_ctx {
         tmap_ok = false;
         n = h = w = ii_stride = npad = lines = box_lines = 0;
         nfeat = 0;
+        lay = WeightLayout{};
     }
     void free_events() {
         for (auto &t : ev_free) for (auto e : t) cudaEventDestroy(e);
@@ -174,7 +181,7 @@ int make_tensor_map(vjb_ctx *c) {
 }
 
 bool shape_fits(const vjb_ctx *c, const SearchShape &s) {
-    return search_smem_bytes(s, c->n) <= (size_t)c->max_smem;
+    return s.warps <= screen_max_warps(s.unroll) && search_smem_bytes(s, c->lay.words) <= (size_t)c->max_smem;
 }
 
 int apply_shape(vjb_ctx *c) {
@@ -184,7 +191,8 @@ int apply_shape(vjb_ctx *c) {
         CK(cudaMalloc(&c->d_bmin, sizeof(float) * c->screen_grid));
         c->bmin_cap = c->screen_grid;
     }
-    c->refine_grid = c->num_sms * 2;
+    c->shortlist_grid = c->num_sms * 2;
+    c->rescan_grid = c->num_sms * 2;
     c->shape_set = true;
     c->drop_graph();
     return VJB_OK;
@@ -192,7 +200,8 @@ int apply_shape(vjb_ctx *c) {
 
 int choose_default_shape(vjb_ctx *c) {
     if (c->shape_set && shape_fits(c, c->shape)) return apply_shape(c);
-    const SearchShape tries[] = {{8, 4, 1}, {8, 3, 1}, {6, 4, 1}, {4, 4, 1}, {4, 3, 1}, {4, 2, 1}, {2, 2, 1}};
+    const SearchShape tries[] = {{12, 3, 1, 2}, {8, 4, 1, 2}, {8, 3, 1, 2}, {8, 2, 1, 2}, {6, 3, 1, 2},
+                                 {4, 4, 1, 2}, {4, 2, 1, 2}, {2, 2, 1, 2}};
     for (const auto &s : tries)
         if (shape_fits(c, s)) {
             c->shape = s;
@@ -251,16 +260,25 @@ int collect_timing(vjb_ctx *c) {
 
 // The launches of one round (Sec. 2.3 steps 2-4, with step 1 of the next
 // round).  `ev` (may be NULL) brackets the search kernel and the round.
+int enqueue_update(vjb_ctx *c) {
+    CK(launch_update_a(c->d_rows, c->npad, c->lay, c->d_ii, c->ii_stride, c->w, c->d_feat, c->d_y,
+                       c->d_w, c->d_miss, c->d_partials, c->d_rs, c->d_stumps, c->stump_cap,
+                       c->d_last, c->stream));
+    CK(launch_update_b(c->lay, c->d_y, c->d_w, c->d_v, c->d_miss, c->d_partials, c->d_rs, c->stream));
+    return VJB_OK;
+}
+
 int enqueue_round(vjb_ctx *c, const EventTriple *ev, unsigned rec_flags) {
     if (ev) CK(cudaEventRecordWithFlags((*ev)[0], c->stream, rec_flags));
-    CK(launch_screen(&c->tmap, c->d_v, c->n, c->lines, c->box_lines, c->nfeat, c->shape,
+    CK(launch_screen(&c->tmap, c->d_v, c->lay, c->lines, c->box_lines, c->nfeat, c->shape,
                      c->screen_grid, c->d_rs, c->d_ferr, c->d_bmin, c->stream));
     if (ev) CK(cudaEventRecordWithFlags((*ev)[1], c->stream, rec_flags));
-    CK(launch_refine(c->d_rows, c->npad, c->n, c->nfeat, c->d_v, c->d_rs, c->d_ferr, c->d_bmin,
-                     c->screen_grid, c->d_cand, c->refine_grid, c->stream));
-    CK(launch_finalize(c->d_rows, c->npad, c->n, c->d_ii, c->ii_stride, c->w, c->d_feat, c->nfeat,
-                       c->d_y, c->d_w, c->d_v, c->d_rs, c->d_cand, c->d_stumps, c->stump_cap,
-                       c->d_last, c->stream));
+    CK(launch_shortlist(c->nfeat, c->d_rs, c->d_ferr, c->d_bmin, c->screen_grid, c->d_cand_ids,
+                        c->shortlist_grid, c->stream));
+    CK(launch_rescan(c->d_rows, c->npad, c->d_v, c->lay, c->d_rs, c->d_cand_ids, c->d_cand,
+                     c->rescan_grid, c->stream));
+    int rc = enqueue_update(c);
+    if (rc) return rc;
     if (ev) CK(cudaEventRecordWithFlags((*ev)[2], c->stream, rec_flags));
     return VJB_OK;
 }
@@ -322,7 +340,7 @@ int read_state(vjb_ctx *c, RoundState *rs) {
 
 int device_flags_error(const RoundState &rs) {
     return fail(VJB_EDEVICE, "kernel error flags 0x%x (1 = wait timeout, 2 = no candidate, 4 = bad weights, 8 = bad table)",
-                rs.flags);
+                rs.flags | 0);
 }
 
 int validate_labels(const uint8_t *y, int n) {
@@ -365,7 +383,11 @@ int load_common(vjb_ctx *c, const uint8_t *pixels, const uint8_t *labels, int32_
         CK(cudaMalloc(&c->d_y, (size_t)n));
         CK(cudaMalloc(&c->d_w, sizeof(float) * n));
         CK(cudaMalloc(&c->d_wtmp, sizeof(float) * n));
-        CK(cudaMalloc(&c->d_v, sizeof(float) * (n + 1)));
+        c->lay = make_layout(n, true);
+        CK(cudaMalloc(&c->d_v, sizeof(float) * c->lay.words));
+        CK(cudaMemset(c->d_v, 0, sizeof(float) * c->lay.words));
+        CK(cudaMalloc(&c->d_miss, (size_t)n));
+        CK(cudaMalloc(&c->d_partials, sizeof(double) * 3 * kUpdateMaxCtas));
         CK(cudaMalloc(&c->d_rs, sizeof(RoundState)));
         CK(cudaMalloc(&c->d_last, sizeof(vjb_stump)));
         rc = ensure_stump_cap(c, 1024);
@@ -377,7 +399,7 @@ int load_common(vjb_ctx *c, const uint8_t *pixels, const uint8_t *labels, int32_
     CK(cudaMemcpyAsync(c->d_y, hy.data(), (size_t)n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->d_rs, 0, sizeof(RoundState), c->stream));
     CK(cudaMemsetAsync(c->d_last, 0, sizeof(vjb_stump), c->stream));
-    CK(launch_init_weights(c->d_y, n, nullptr, c->d_w, c->d_v, c->d_rs, c->stream));
+    CK(launch_init_weights(c->d_y, c->lay, nullptr, c->d_w, c->d_v, c->d_rs, c->stream));
     c->launches += 1;
     CK(cudaStreamSynchronize(c->stream));
     c->stage = kStageLoaded;
@@ -420,7 +442,7 @@ int prepare_tables(vjb_ctx *c) {
         cudaError_t e = launch_feature_values(c->d_ii, c->ii_stride, c->n, c->w, c->d_feat, f0, nf,
                                               d_vals, c->stream);
         if (e == cudaSuccess)
-            e = launch_sort_rows(d_vals, c->n, nf, c->d_rows + (size_t)f0 * c->npad, c->npad, c->stream);
+            e = launch_sort_rows(d_vals, c->lay, nf, c->d_rows + (size_t)f0 * c->npad, c->npad, c->stream);
         if (e != cudaSuccess) err = fail(VJB_ECUDA, "prepare launch failed: %s", cudaGetErrorString(e));
         c->launches += 2;
     }
@@ -429,7 +451,7 @@ int prepare_tables(vjb_ctx *c) {
     if (err) return err;
     if (se != cudaSuccess) return fail(VJB_ECUDA, "prepare failed: %s", cudaGetErrorString(se));
     // the search kernels gather through the table without bounds checks: validate it once
-    CK(launch_check_rows(c->d_rows, c->nfeat, c->n, c->npad, flags_ptr(c), c->num_sms * 8, c->stream));
+    CK(launch_check_rows(c->d_rows, c->nfeat, c->lay, c->npad, flags_ptr(c), c->num_sms * 8, c->stream));
     c->launches += 1;
     RoundState rs;
     int rc = read_state(c, &rs);
@@ -437,6 +459,7 @@ int prepare_tables(vjb_ctx *c) {
     if (rs.flags) return device_flags_error(rs);
     if (!c->d_ferr) CK(cudaMalloc(&c->d_ferr, sizeof(float) * c->nfeat));
     if (!c->d_cand) CK(cudaMalloc(&c->d_cand, sizeof(Candidate) * c->nfeat));
+    if (!c->d_cand_ids) CK(cudaMalloc(&c->d_cand_ids, sizeof(int32_t) * c->nfeat));
     if (!c->tmap_ok) {
         rc = make_tensor_map(c);
         if (rc) return rc;
@@ -646,7 +669,7 @@ int vjb_set_weights(vjb_ctx *c, const float *wts) {
     int rc = set_dev(c);
     if (rc) return rc;
     CK(cudaMemcpyAsync(c->d_wtmp, wts, sizeof(float) * c->n, cudaMemcpyHostToDevice, c->stream));
-    CK(launch_init_weights(c->d_y, c->n, c->d_wtmp, c->d_w, c->d_v, c->d_rs, c->stream));
+    CK(launch_init_weights(c->d_y, c->lay, c->d_wtmp, c->d_w, c->d_v, c->d_rs, c->stream));
     c->launches += 1;
     CK(cudaStreamSynchronize(c->stream));
     return VJB_OK;
@@ -669,10 +692,9 @@ int vjb_force_stump(vjb_ctx *c, int32_t feature, int32_t threshold, int32_t pola
         int32_t f4[4] = {1, feature, threshold, polarity};
         char *dst = reinterpret_cast<char *>(c->d_rs) + offsetof(RoundState, forced);
         CK(cudaMemcpyAsync(dst, f4, sizeof f4, cudaMemcpyHostToDevice, c->stream));
-        CK(launch_finalize(c->d_rows, c->npad, c->n, c->d_ii, c->ii_stride, c->w, c->d_feat, c->nfeat,
-                           c->d_y, c->d_w, c->d_v, c->d_rs, c->d_cand, c->d_stumps, c->stump_cap,
-                           c->d_last, c->stream));
-        c->launches += 1;
+        rc = enqueue_update(c);
+        if (rc) return rc;
+        c->launches += 2;
         rc = read_state(c, &rs);
         if (rc) return rc;
     }
@@ -694,6 +716,8 @@ int vjb_get_info(vjb_ctx *c, vjb_info *out) {
     out->kernel_warps = c->shape.warps;
     out->kernel_stages = c->shape.stages;
     out->kernel_ctas = c->screen_grid;
+    out->kernel_unroll = c->shape.unroll;
+    out->dual_weights = c->lay.dual;
     out->search_bytes = 2.0 * (double)c->nfeat * (double)c->n;
     out->launches = c->launches;
     if (c->stage >= kStageLoaded) {
@@ -760,6 +784,15 @@ int vjb_sorted_rows(vjb_ctx *c, int64_t f0, int64_t nf, uint16_t *out) {
                          sizeof(uint16_t) * c->npad, sizeof(uint16_t) * c->n, (size_t)nf,
                          cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    // the device table names samples through words of the weight array
+    if (c->lay.dual) {
+        const size_t cnt = (size_t)nf * c->n;
+        for (size_t k = 0; k < cnt; ++k) {
+            const uint16_t e = out[k];
+            const int word = e & kIndexMask;
+            out[k] = (uint16_t)((e & kFlagBit) | word_to_sample(word, c->lay));
+        }
+    }
     return VJB_OK;
 }
 
@@ -774,18 +807,23 @@ int vjb_screen_errors(vjb_ctx *c, float *out) {
     return VJB_OK;
 }
 
-int vjb_set_search_shape(vjb_ctx *c, int32_t warps, int32_t stages, int32_t ctas_per_sm) {
+int vjb_set_search_shape(vjb_ctx *c, int32_t warps, int32_t stages, int32_t ctas_per_sm,
+                         int32_t unroll) {
     g_err[0] = 0;
     if (!c) return fail(VJB_EINVAL, "context is NULL");
     SearchShape s = c->shape;
     if (warps) s.warps = warps;
     if (stages) s.stages = stages;
     if (ctas_per_sm) s.ctas_per_sm = ctas_per_sm;
-    if (s.warps < 1 || s.warps > 16 || s.stages < 2 || s.stages > 8 || s.ctas_per_sm < 1 || s.ctas_per_sm > 4)
-        return fail(VJB_EINVAL, "search shape (%d warps, %d stages, %d CTAs/SM) out of range", s.warps, s.stages, s.ctas_per_sm);
+    if (unroll) s.unroll = unroll;
+    if (s.warps < 1 || s.warps > 16 || s.stages < 2 || s.stages > 8 || s.ctas_per_sm < 1 || s.ctas_per_sm > 4 ||
+        (s.unroll != 1 && s.unroll != 2 && s.unroll != 4) || s.warps > screen_max_warps(s.unroll))
+        return fail(VJB_EINVAL, "search shape (%d warps, %d stages, %d CTAs/SM, unroll %d) out of range",
+                    s.warps, s.stages, s.ctas_per_sm, s.unroll);
     if (c->n > 0 && !shape_fits(c, s))
-        return fail(VJB_EINVAL, "search shape needs %zu bytes of shared memory (limit %d)", search_smem_bytes(s, c->n), c->max_smem);
-    if (c->n > 0 && screen_occupancy(s, c->n) < s.ctas_per_sm)
+        return fail(VJB_EINVAL, "search shape needs %zu bytes of shared memory (limit %d)",
+                    search_smem_bytes(s, c->lay.words), c->max_smem);
+    if (c->n > 0 && screen_occupancy(s, c->lay.words) < s.ctas_per_sm)
         return fail(VJB_EINVAL, "%d CTAs per SM of this shape do not fit one SM", s.ctas_per_sm);
     int rc = set_dev(c);
     if (rc) return rc;

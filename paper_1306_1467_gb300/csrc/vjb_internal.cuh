@@ -15,25 +15,55 @@ struct DevFeature {
     uint8_t type, x, y, w, h, pad0, pad1, pad2;
 };
 
+// Where the signed weights v_i (+w_i for a face, -w_i for a non-face) live.
+// Table entries are word offsets into this array.  With two copies, copy A
+// holds v_i at word i and copy B at word off_b + rot(i), where rot rotates
+// each aligned block of 32 samples by 13 * (block number): the two copies put
+// a sample in unrelated shared-memory banks, and the sort kernel picks, for
+// every group of 32 entries one gather instruction reads, the copy of each
+// entry that balances the banks.  Word n holds 0 and is the padding entry.
+struct WeightLayout {
+    int n;
+    int dual;    // 1: two copies, 0: copy A only
+    int off_b;   // first word of copy B (a multiple of 32), 0 without it
+    int words;   // array length in floats
+};
+
+__host__ __device__ __forceinline__ int rot_b(int i) {
+    return (i & ~31) | ((i + 13 * (i >> 5)) & 31);
+}
+__host__ __device__ __forceinline__ int unrot_b(int r) {
+    return (r & ~31) | ((r - 13 * (r >> 5)) & 31);
+}
+// Sample named by a table word (n for the padding word).
+__host__ __device__ __forceinline__ int word_to_sample(int word, const WeightLayout &L) {
+    if (L.dual && word >= L.off_b) return unrot_b(word - L.off_b);
+    return word;
+}
+
 // Round state that lives on the device between the kernels of a round.
 struct RoundState {
     double t_pos;        // FP64 sum of the FP32 weights of faces
     double t_neg;        // same for non-faces
     double weight_sum;   // t_pos + t_neg
+    double scale_hit;    // beta / updated total: factor for correctly classified samples
+    double scale_miss;   // 1 / updated total: factor for misclassified samples
     int32_t status;      // VJB_OK or VJB_DONE_*
     int32_t rounds;      // stumps kept so far
-    int32_t cand_count;  // shortlist entries written by the refine kernel
+    int32_t cand_count;  // shortlisted features of the current search
     int32_t last_cands;  // shortlist size of the last finished search
     int32_t flags;       // error flags (kFlag*)
     float screen_min;    // smallest screened error of the last search
     int32_t forced;      // 1 while a host-given stump replaces the search
     int32_t forced_feature, forced_threshold, forced_polarity;
+    int32_t win_feature, win_split, win_polarity;  // the round's stump
+    uint32_t done_rescan, done_update_a, done_update_b;  // last-CTA counters
     int32_t pad;
 };
 
 // Device error flags.
 constexpr int32_t kFlagWaitTimeout = 1;   // an mbarrier wait gave up
-constexpr int32_t kFlagNoCandidate = 2;   // the refine kernel found no feature
+constexpr int32_t kFlagNoCandidate = 2;   // the shortlist was empty
 constexpr int32_t kFlagBadWeights = 4;    // weight total not positive / finite
 constexpr int32_t kFlagBadTable = 8;      // a sorted-table entry out of range
 
@@ -61,13 +91,19 @@ constexpr uint16_t kIndexMask = 0x7FFFu;
 // compensated.  It is twice a bound on the screening error (see k_search.cu).
 constexpr float kScreenMarginUlps = 64.0f;
 
+// Partials of the multi-CTA update kernels (one slot per CTA).
+constexpr int kUpdateThreads = 256;
+constexpr int kUpdateMaxCtas = 4096;
+
 struct SearchShape {
     int warps;        // consumer warps per CTA
     int stages;       // TMA stages per warp
     int ctas_per_sm;
+    int unroll;       // 512-entry units a warp works on together (1, 2 or 4)
 };
 
-size_t search_smem_bytes(const SearchShape &s, int n);
+size_t search_smem_bytes(const SearchShape &s, int words);
+WeightLayout make_layout(int n, bool allow_dual);
 
 // Launchers (each returns the launch error).
 cudaError_t launch_integral(const uint8_t *px, int n, int h, int w, int32_t *ii_t, int ii_stride,
@@ -75,22 +111,28 @@ cudaError_t launch_integral(const uint8_t *px, int n, int h, int w, int32_t *ii_
 cudaError_t launch_feature_values(const int32_t *ii_t, int ii_stride, int n, int w,
                                   const DevFeature *feat, int64_t f0, int64_t nf, int32_t *out,
                                   cudaStream_t st);
-cudaError_t launch_sort_rows(const int32_t *vals, int n, int64_t nf, uint16_t *rows, int npad,
-                             cudaStream_t st);
-cudaError_t launch_check_rows(const uint16_t *rows, int64_t nfeat, int n, int npad, int32_t *flags,
-                              int grid, cudaStream_t st);
-cudaError_t launch_init_weights(const uint8_t *y, int n, const float *w_in, float *w, float *v,
-                                RoundState *rs, cudaStream_t st);
-cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, int n, int lines_per_row,
-                          int box_lines, int64_t nfeat, const SearchShape &shape, int grid,
-                          RoundState *rs, float *ferr, float *bmin, cudaStream_t st);
-cudaError_t launch_refine(const uint16_t *rows, int npad, int n, int64_t nfeat, const float *v,
-                          RoundState *rs, const float *ferr, const float *bmin, int nbmin,
-                          Candidate *cands, int grid, cudaStream_t st);
-cudaError_t launch_finalize(const uint16_t *rows, int npad, int n, const int32_t *ii_t,
-                            int ii_stride, int w, const DevFeature *feat, int64_t nfeat,
-                            const uint8_t *y, float *wts, float *v, RoundState *rs,
-                            const Candidate *cands, vjb_stump *stumps, int stump_cap,
-                            vjb_stump *last, cudaStream_t st);
+cudaError_t launch_sort_rows(const int32_t *vals, const WeightLayout &L, int64_t nf, uint16_t *rows,
+                             int npad, cudaStream_t st);
+cudaError_t launch_check_rows(const uint16_t *rows, int64_t nfeat, const WeightLayout &L, int npad,
+                              int32_t *flags, int grid, cudaStream_t st);
+cudaError_t launch_init_weights(const uint8_t *y, const WeightLayout &L, const float *w_in,
+                                float *w, float *v, RoundState *rs, cudaStream_t st);
+cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, const WeightLayout &L,
+                          int lines_per_row, int box_lines, int64_t nfeat, const SearchShape &shape,
+                          int grid, RoundState *rs, float *ferr, float *bmin, cudaStream_t st);
+cudaError_t launch_shortlist(int64_t nfeat, RoundState *rs, const float *ferr, const float *bmin,
+                             int nbmin, int32_t *cand_ids, int grid, cudaStream_t st);
+cudaError_t launch_rescan(const uint16_t *rows, int npad, const float *v, const WeightLayout &L,
+                          RoundState *rs, const int32_t *cand_ids, Candidate *cands, int grid,
+                          cudaStream_t st);
+cudaError_t launch_update_a(const uint16_t *rows, int npad, const WeightLayout &L,
+                            const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
+                            const uint8_t *y, const float *wts, uint8_t *miss, double *partials,
+                            RoundState *rs, vjb_stump *stumps, int stump_cap, vjb_stump *last,
+                            cudaStream_t st);
+cudaError_t launch_update_b(const WeightLayout &L, const uint8_t *y, float *wts, float *v,
+                            const uint8_t *miss, double *partials, RoundState *rs,
+                            cudaStream_t st);
+int update_grid(int n);
 
 }  // namespace vjb

@@ -52,8 +52,9 @@ class Info(C.Structure):
                 ("t_pos", C.c_double), ("t_neg", C.c_double), ("weight_sum", C.c_double),
                 ("screen_min", C.c_float), ("candidates", C.c_int32),
                 ("device_flags", C.c_int32), ("kernel_warps", C.c_int32),
-                ("kernel_stages", C.c_int32), ("kernel_ctas", C.c_int32), ("pad", C.c_int32),
-                ("search_bytes", C.c_double), ("launches", C.c_int64)]
+                ("kernel_stages", C.c_int32), ("kernel_ctas", C.c_int32),
+                ("kernel_unroll", C.c_int32), ("search_bytes", C.c_double),
+                ("launches", C.c_int64), ("dual_weights", C.c_int32), ("pad", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
@@ -88,7 +89,7 @@ SIGNATURES = {
     "vjb_feature_values": (C.c_int, [_P, _I64, _I64, _P]),
     "vjb_sorted_rows": (C.c_int, [_P, _I64, _I64, _P]),
     "vjb_screen_errors": (C.c_int, [_P, _P]),
-    "vjb_set_search_shape": (C.c_int, [_P, _I32, _I32, _I32]),
+    "vjb_set_search_shape": (C.c_int, [_P, _I32, _I32, _I32, _I32]),
     "vjb_set_timing": (C.c_int, [_P, _I32]),
     "vjb_get_timing": (C.c_int, [_P, _P]),
     "vjb_screen_noalloc": (C.c_int, [_P, _P, _I32, _I32, _I64, C.c_double, C.c_double, _I32,
@@ -246,8 +247,9 @@ class Trainer:
         self._check(self._lib.vjb_get_info(self._h, C.byref(i)))
         return i.as_dict()
 
-    def set_search_shape(self, warps: int = 0, stages: int = 0, ctas_per_sm: int = 0):
-        self._check(self._lib.vjb_set_search_shape(self._h, int(warps), int(stages), int(ctas_per_sm)))
+    def set_search_shape(self, warps: int = 0, stages: int = 0, ctas_per_sm: int = 0, unroll: int = 0):
+        self._check(self._lib.vjb_set_search_shape(self._h, int(warps), int(stages), int(ctas_per_sm),
+                                                   int(unroll)))
 
     def set_timing(self, enable: bool = True):
         """Enable (and reset) CUDA-event timing of every round's search kernel."""
