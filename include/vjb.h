@@ -90,6 +90,8 @@ typedef struct {
     int32_t kernel_stages;    /* search kernel: TMA stages per warp             */
     int32_t kernel_ctas;      /* search kernel: CTAs in the grid                */
     int32_t kernel_unroll;    /* search kernel: 512-entry units a warp works on together */
+    int32_t kernel_box_lines; /* search kernel: 128-byte lines per TMA box                */
+    int32_t pad0;
     double  search_bytes;     /* algorithmic bytes one search reads: 2 * F * N  */
     int64_t launches;         /* kernels this context has launched so far       */
     int32_t dual_weights;     /* 1: the search gathers from two bank-balanced weight copies */
@@ -212,13 +214,19 @@ int vjb_sorted_rows(vjb_ctx *ctx, int64_t f0, int64_t nf, uint16_t *out);
 int vjb_screen_errors(vjb_ctx *ctx, float *out);
 
 /* ---- tuning ------------------------------------------------------------------
- * Launch shape of the search kernel: consumer warps per CTA (1-16; at most 8
- * with unroll 4), TMA stages per warp (2-8), CTAs per SM (1-4) and the number
- * of 512-entry units a warp works on together (1, 2 or 4); 0 keeps the
- * current value.  Shapes whose shared memory does not fit are rejected with
+ * Launch shape of the search kernel.  Fields set to 0 keep their current
+ * value.  Shapes whose shared memory does not fit one SM are rejected with
  * VJB_EINVAL.  Takes effect from the next round. */
-int vjb_set_search_shape(vjb_ctx *ctx, int32_t warps, int32_t stages, int32_t ctas_per_sm,
-                         int32_t unroll);
+typedef struct {
+    int32_t warps;        /* consumer warps per CTA: 1-16 (1-8 with unroll 4)      */
+    int32_t stages;       /* TMA stages per warp: 2-8                              */
+    int32_t ctas_per_sm;  /* 1-4                                                   */
+    int32_t unroll;       /* 512-entry units a warp works on together: 1, 2 or 4   */
+    int32_t box_lines;    /* 128-byte lines per TMA box (stage): 8, 16 or 32       */
+} vjb_search_shape;
+
+int vjb_set_search_shape(vjb_ctx *ctx, const vjb_search_shape *shape);
+int vjb_get_search_shape(vjb_ctx *ctx, vjb_search_shape *out);
 
 /* ---- timing ------------------------------------------------------------------
  * vjb_set_timing: enable (1) or disable (0) event timing of rounds; enabling

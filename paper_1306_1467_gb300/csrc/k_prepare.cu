@@ -234,8 +234,7 @@ __global__ void __launch_bounds__(kSortThreads, 1)
             // for a 512-entry unit u and a slot j in 0..15, the 32 entries at
             // u*512 + 16k + j (k = 0..31).  For each such group, greedily put each
             // entry in the less loaded of its two banks (copy A: i mod 32, copy
-            // B: rot(i) mod 32), then move entries out of the fullest bank while
-            // that lowers the maximum.
+            // B: rot(i) mod 32), then let entries move to a lighter bank.
             uint32_t *gchoice = hist + kRadix * kSortWarps;  // one mask per group
             uint8_t *ld = reinterpret_cast<uint8_t *>(hist) + (size_t)threadIdx.x * 32;
             const int ngroups = (npad + kUnitElems - 1) / kUnitElems * 16;
@@ -258,26 +257,22 @@ __global__ void __launch_bounds__(kSortThreads, 1)
                     if (ld[bb] < ld[ba]) { ld[bb]++; mask |= 1u << k; }
                     else ld[ba]++;
                 }
-                for (int it = 0; it < 32; ++it) {
-                    int m = 0;
-                    for (int b = 0; b < 32; ++b) m = max(m, (int)ld[b]);
-                    bool moved = false;
-                    for (int k = 0; k < 32 && !moved; ++k) {
+                // two passes of single moves: an entry leaves its bank when the
+                // other one is at least two entries lighter
+                for (int pass = 0; pass < 2; ++pass)
+                    for (int k = 0; k < 32; ++k) {
                         const int p = u * kUnitElems + 16 * k + j;
                         if (p >= n || p >= npad) break;
                         const int i = sidx[p];
                         const int ba = i & 31, bb = rot_b(i) & 31;
                         const bool onb = (mask >> k) & 1u;
                         const int cur = onb ? bb : ba, oth = onb ? ba : bb;
-                        if (ld[cur] == m && ld[oth] + 1 < m) {
+                        if (ld[cur] > ld[oth] + 1) {
                             ld[cur]--;
                             ld[oth]++;
                             mask ^= 1u << k;
-                            moved = true;
                         }
                     }
-                    if (!moved) break;
-                }
                 gchoice[g] = mask;
             }
             __syncthreads();

@@ -51,7 +51,7 @@ __host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return
 size_t search_smem_bytes(const SearchShape &s, int words) {
     size_t b = align_up((size_t)words * 4, 16);
     b += 1024;  // alignment of the rings to 1 KiB
-    b += (size_t)s.warps * s.stages * kStageBytes;
+    b += (size_t)s.warps * s.stages * s.box_lines * kLineBytes;
     b += (size_t)s.warps * s.stages * 8;
     b += (size_t)s.warps * 4 + 16;
     return b;
@@ -157,19 +157,20 @@ __device__ __forceinline__ void screen_units(uint32_t sbase, int u0, int lane, i
 template <int U>
 __global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
     k_screen(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ v, int words,
-             int pad_word, int lines_per_row, int box_lines, int64_t nfeat, int stages,
-             RoundState *rs, float *__restrict__ ferr, float *__restrict__ bmin) {
+             int pad_word, int lines_per_row, int box_lines, int stage_lines, int64_t nfeat,
+             int stages, RoundState *rs, float *__restrict__ ferr, float *__restrict__ bmin) {
     if (rs->status != VJB_OK) return;
     extern __shared__ __align__(16) float sv[];  // weights at the base of dynamic shared memory
     const int nw = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t sv32 = smem_u32(sv);
+    const uint32_t stage_bytes = (uint32_t)stage_lines * kLineBytes;  // a multiple of 1 KiB
     const uint32_t ring0 = (uint32_t)align_up(sv32 + (uint32_t)words * 4u, 1024);
-    const uint32_t bars0 = ring0 + (uint32_t)(nw * stages * kStageBytes);
+    const uint32_t bars0 = ring0 + (uint32_t)nw * stages * stage_bytes;
     float *wbest = reinterpret_cast<float *>(reinterpret_cast<char *>(sv) + (bars0 + nw * stages * 8 - sv32));
 
     for (int i = threadIdx.x; i < words; i += blockDim.x) sv[i] = v[i];
-    const uint32_t ring_w = ring0 + (uint32_t)(warp * stages * kStageBytes);
+    const uint32_t ring_w = ring0 + (uint32_t)warp * stages * stage_bytes;
     const uint32_t bar_w = bars0 + (uint32_t)(warp * stages * 8);
     if (lane == 0) {
         for (int s = 0; s < stages; ++s) mbar_init(bar_w + 8 * s, 1);
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
         const int stage = (int)(seq % stages);
         const uint32_t bar = bar_w + 8u * stage;
         mbar_arrive_expect_tx(bar, tx);
-        tma_load_3d(ring_w + (uint32_t)stage * kStageBytes, &tmap, 0, c * box_lines, (int32_t)f, bar);
+        tma_load_3d(ring_w + (uint32_t)stage * stage_bytes, &tmap, 0, c * box_lines, (int32_t)f, bar);
     };
     if (lane == 0) {
         const int64_t pro = total < stages ? total : stages;
@@ -215,11 +216,10 @@ __global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
                 break;
             }
             const int lines_here = min(box_lines, lines_per_row - c * box_lines);
-            const uint32_t sbase = ring_w + (uint32_t)stage * kStageBytes;
-            if (lines_here == kBoxLinesMax) {
-#pragma unroll
-                for (int u0 = 0; u0 < kBoxLinesMax / 8; u0 += U)
-                    screen_units<U>(sbase, u0, lane, kBoxLinesMax, pad2, sv, chi, clo, MX, MN);
+            const uint32_t sbase = ring_w + (uint32_t)stage * stage_bytes;
+            if (lines_here == box_lines && (box_lines & (8 * U - 1)) == 0) {
+                for (int u0 = 0; u0 < box_lines / 8; u0 += U)
+                    screen_units<U>(sbase, u0, lane, box_lines, pad2, sv, chi, clo, MX, MN);
             } else {
                 const int units = (lines_here + 7) >> 3;
                 for (int u0 = 0; u0 < units; u0 += U)
@@ -268,16 +268,16 @@ cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, const WeightL
     const int threads = shape.warps * 32;
     switch (shape.unroll) {
     case 1:
-        k_screen<1><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines, nfeat,
-                                               shape.stages, rs, ferr, bmin);
+        k_screen<1><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines,
+                                               shape.box_lines, nfeat, shape.stages, rs, ferr, bmin);
         break;
     case 4:
-        k_screen<4><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines, nfeat,
-                                               shape.stages, rs, ferr, bmin);
+        k_screen<4><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines,
+                                               shape.box_lines, nfeat, shape.stages, rs, ferr, bmin);
         break;
     default:
-        k_screen<2><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines, nfeat,
-                                               shape.stages, rs, ferr, bmin);
+        k_screen<2><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines,
+                                               shape.box_lines, nfeat, shape.stages, rs, ferr, bmin);
     }
     return cudaGetLastError();
 }
@@ -816,7 +816,8 @@ extern "C" int vjb_screen_noalloc(const uint16_t *rows, const float *v, int32_t 
         }
     }
     const int grid = ctas ? ctas : std::min(D.num_sms, kNoAllocMaxCtas);
-    const SearchShape tries[] = {{8, 4, 1}, {8, 3, 1}, {4, 4, 1}, {4, 2, 1}, {2, 2, 1}};
+    const SearchShape tries[] = {{8, 4, 1, 1, 32}, {8, 3, 1, 1, 32}, {4, 4, 1, 1, 32}, {4, 2, 1, 1, 32},
+                                 {2, 2, 1, 1, 32}};
     const SearchShape *shape = nullptr;
     for (const auto &s : tries)
         if (noalloc_smem_bytes(s, n) <= (size_t)D.max_smem) { shape = &s; break; }

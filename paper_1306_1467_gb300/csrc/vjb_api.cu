@@ -92,7 +92,7 @@ struct vjb_ctx {
     std::vector<vjb_feature> feats;
     CUtensorMap tmap;
     bool tmap_ok = false;
-    SearchShape shape{8, 4, 1, 2};
+    SearchShape shape{12, 2, 1, 2, 32};
     bool shape_set = false;
     int screen_grid = 0, shortlist_grid = 0, rescan_grid = 0;
 
@@ -184,8 +184,18 @@ bool shape_fits(const vjb_ctx *c, const SearchShape &s) {
     return s.warps <= screen_max_warps(s.unroll) && search_smem_bytes(s, c->lay.words) <= (size_t)c->max_smem;
 }
 
+int make_tensor_map(vjb_ctx *c);
+
 int apply_shape(vjb_ctx *c) {
     c->screen_grid = c->num_sms * c->shape.ctas_per_sm;
+    const int box = std::min(c->shape.box_lines, c->lines);
+    if (box != c->box_lines || !c->tmap_ok) {
+        c->box_lines = box;
+        if (c->d_rows) {
+            const int rc = make_tensor_map(c);
+            if (rc) return rc;
+        }
+    }
     if (c->screen_grid > c->bmin_cap) {
         dfree(c->d_bmin);
         CK(cudaMalloc(&c->d_bmin, sizeof(float) * c->screen_grid));
@@ -200,8 +210,10 @@ int apply_shape(vjb_ctx *c) {
 
 int choose_default_shape(vjb_ctx *c) {
     if (c->shape_set && shape_fits(c, c->shape)) return apply_shape(c);
-    const SearchShape tries[] = {{12, 3, 1, 2}, {8, 4, 1, 2}, {8, 3, 1, 2}, {8, 2, 1, 2}, {6, 3, 1, 2},
-                                 {4, 4, 1, 2}, {4, 2, 1, 2}, {2, 2, 1, 2}};
+    // measured on the 24x24 / 15k workload: more warps with two stages beat deeper rings
+    const SearchShape tries[] = {{12, 2, 1, 2, 32}, {16, 2, 1, 2, 16}, {8, 3, 1, 2, 32}, {8, 2, 1, 2, 32},
+                                 {6, 3, 1, 2, 32}, {4, 4, 1, 2, 32}, {4, 2, 1, 2, 32}, {2, 2, 1, 2, 16},
+                                 {2, 2, 1, 1, 8}};
     for (const auto &s : tries)
         if (shape_fits(c, s)) {
             c->shape = s;
@@ -430,7 +442,7 @@ int prepare_tables(vjb_ctx *c) {
         CK(cudaMemcpy(c->d_feat, df.data(), sizeof(DevFeature) * df.size(), cudaMemcpyHostToDevice));
         c->npad = (c->n + kLineElems - 1) / kLineElems * kLineElems;
         c->lines = c->npad / kLineElems;
-        c->box_lines = std::min(kBoxLinesMax, c->lines);
+        c->box_lines = 0;  // set with the search shape
     }
     if (!c->d_rows) CK(cudaMalloc(&c->d_rows, sizeof(uint16_t) * (size_t)c->nfeat * c->npad));
     const int64_t tile = std::max<int64_t>(1, std::min<int64_t>(c->nfeat, (int64_t(1) << 28) / c->n));
@@ -460,11 +472,7 @@ int prepare_tables(vjb_ctx *c) {
     if (!c->d_ferr) CK(cudaMalloc(&c->d_ferr, sizeof(float) * c->nfeat));
     if (!c->d_cand) CK(cudaMalloc(&c->d_cand, sizeof(Candidate) * c->nfeat));
     if (!c->d_cand_ids) CK(cudaMalloc(&c->d_cand_ids, sizeof(int32_t) * c->nfeat));
-    if (!c->tmap_ok) {
-        rc = make_tensor_map(c);
-        if (rc) return rc;
-    }
-    if (!c->d_bmin) {
+    if (!c->d_bmin || !c->tmap_ok) {
         rc = choose_default_shape(c);
         if (rc) return rc;
     }
@@ -717,6 +725,7 @@ int vjb_get_info(vjb_ctx *c, vjb_info *out) {
     out->kernel_stages = c->shape.stages;
     out->kernel_ctas = c->screen_grid;
     out->kernel_unroll = c->shape.unroll;
+    out->kernel_box_lines = c->box_lines;
     out->dual_weights = c->lay.dual;
     out->search_bytes = 2.0 * (double)c->nfeat * (double)c->n;
     out->launches = c->launches;
@@ -807,19 +816,20 @@ int vjb_screen_errors(vjb_ctx *c, float *out) {
     return VJB_OK;
 }
 
-int vjb_set_search_shape(vjb_ctx *c, int32_t warps, int32_t stages, int32_t ctas_per_sm,
-                         int32_t unroll) {
+int vjb_set_search_shape(vjb_ctx *c, const vjb_search_shape *in) {
     g_err[0] = 0;
-    if (!c) return fail(VJB_EINVAL, "context is NULL");
+    if (!c || !in) return fail(VJB_EINVAL, "NULL argument");
     SearchShape s = c->shape;
-    if (warps) s.warps = warps;
-    if (stages) s.stages = stages;
-    if (ctas_per_sm) s.ctas_per_sm = ctas_per_sm;
-    if (unroll) s.unroll = unroll;
+    if (in->warps) s.warps = in->warps;
+    if (in->stages) s.stages = in->stages;
+    if (in->ctas_per_sm) s.ctas_per_sm = in->ctas_per_sm;
+    if (in->unroll) s.unroll = in->unroll;
+    if (in->box_lines) s.box_lines = in->box_lines;
     if (s.warps < 1 || s.warps > 16 || s.stages < 2 || s.stages > 8 || s.ctas_per_sm < 1 || s.ctas_per_sm > 4 ||
-        (s.unroll != 1 && s.unroll != 2 && s.unroll != 4) || s.warps > screen_max_warps(s.unroll))
-        return fail(VJB_EINVAL, "search shape (%d warps, %d stages, %d CTAs/SM, unroll %d) out of range",
-                    s.warps, s.stages, s.ctas_per_sm, s.unroll);
+        (s.unroll != 1 && s.unroll != 2 && s.unroll != 4) || s.warps > screen_max_warps(s.unroll) ||
+        (s.box_lines != 8 && s.box_lines != 16 && s.box_lines != 32) || 8 * s.unroll > s.box_lines)
+        return fail(VJB_EINVAL, "search shape (%d warps, %d stages, %d CTAs/SM, unroll %d, box %d lines) out of range",
+                    s.warps, s.stages, s.ctas_per_sm, s.unroll, s.box_lines);
     if (c->n > 0 && !shape_fits(c, s))
         return fail(VJB_EINVAL, "search shape needs %zu bytes of shared memory (limit %d)",
                     search_smem_bytes(s, c->lay.words), c->max_smem);
@@ -830,6 +840,17 @@ int vjb_set_search_shape(vjb_ctx *c, int32_t warps, int32_t stages, int32_t ctas
     c->shape = s;
     c->shape_set = true;
     if (c->stage >= kStagePrepared) return apply_shape(c);
+    return VJB_OK;
+}
+
+int vjb_get_search_shape(vjb_ctx *c, vjb_search_shape *out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(VJB_EINVAL, "NULL argument");
+    out->warps = c->shape.warps;
+    out->stages = c->shape.stages;
+    out->ctas_per_sm = c->shape.ctas_per_sm;
+    out->unroll = c->shape.unroll;
+    out->box_lines = c->shape.box_lines;
     return VJB_OK;
 }
 

@@ -100,6 +100,7 @@ struct SearchShape {
     int stages;       // TMA stages per warp
     int ctas_per_sm;
     int unroll;       // 512-entry units a warp works on together (1, 2 or 4)
+    int box_lines;    // 128-byte lines per TMA box (8, 16 or 32)
 };
 
 size_t search_smem_bytes(const SearchShape &s, int words);

@@ -53,11 +53,17 @@ class Info(C.Structure):
                 ("screen_min", C.c_float), ("candidates", C.c_int32),
                 ("device_flags", C.c_int32), ("kernel_warps", C.c_int32),
                 ("kernel_stages", C.c_int32), ("kernel_ctas", C.c_int32),
-                ("kernel_unroll", C.c_int32), ("search_bytes", C.c_double),
+                ("kernel_unroll", C.c_int32), ("kernel_box_lines", C.c_int32), ("pad0", C.c_int32),
+                ("search_bytes", C.c_double),
                 ("launches", C.c_int64), ("dual_weights", C.c_int32), ("pad", C.c_int32)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
+
+
+class SearchShapeC(C.Structure):
+    _fields_ = [("warps", C.c_int32), ("stages", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("unroll", C.c_int32), ("box_lines", C.c_int32)]
 
 
 class Timing(C.Structure):
@@ -89,7 +95,8 @@ SIGNATURES = {
     "vjb_feature_values": (C.c_int, [_P, _I64, _I64, _P]),
     "vjb_sorted_rows": (C.c_int, [_P, _I64, _I64, _P]),
     "vjb_screen_errors": (C.c_int, [_P, _P]),
-    "vjb_set_search_shape": (C.c_int, [_P, _I32, _I32, _I32, _I32]),
+    "vjb_set_search_shape": (C.c_int, [_P, _P]),
+    "vjb_get_search_shape": (C.c_int, [_P, _P]),
     "vjb_set_timing": (C.c_int, [_P, _I32]),
     "vjb_get_timing": (C.c_int, [_P, _P]),
     "vjb_screen_noalloc": (C.c_int, [_P, _P, _I32, _I32, _I64, C.c_double, C.c_double, _I32,
@@ -247,9 +254,16 @@ class Trainer:
         self._check(self._lib.vjb_get_info(self._h, C.byref(i)))
         return i.as_dict()
 
-    def set_search_shape(self, warps: int = 0, stages: int = 0, ctas_per_sm: int = 0, unroll: int = 0):
-        self._check(self._lib.vjb_set_search_shape(self._h, int(warps), int(stages), int(ctas_per_sm),
-                                                   int(unroll)))
+    def set_search_shape(self, warps: int = 0, stages: int = 0, ctas_per_sm: int = 0, unroll: int = 0,
+                         box_lines: int = 0):
+        """Launch shape of the search kernel; 0 keeps a field's current value."""
+        sh = SearchShapeC(int(warps), int(stages), int(ctas_per_sm), int(unroll), int(box_lines))
+        self._check(self._lib.vjb_set_search_shape(self._h, C.byref(sh)))
+
+    def search_shape(self) -> dict:
+        sh = SearchShapeC()
+        self._check(self._lib.vjb_get_search_shape(self._h, C.byref(sh)))
+        return {k: getattr(sh, k) for k, _ in sh._fields_}
 
     def set_timing(self, enable: bool = True):
         """Enable (and reset) CUDA-event timing of every round's search kernel."""
