@@ -72,8 +72,8 @@ cudaError_t launch_feature_values(const int32_t *ii_t, int ii_stride, int n, int
 constexpr int kSortThreads = 1024;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadix = 256;
-// Gather groups of a row with two weight copies (n <= 16352): at most 32
-// units of 512 entries x 16 slots.  Their masks sit after the histogram and
+// Gather groups of a row with two weight copies (n <= 16352): one per entry
+// of a lane run, at most 16384 / 32.  Their masks sit after the histogram and
 // the per-thread bank loads (32 bytes each) reuse the histogram space.
 constexpr int kMaxGroups = 512;
 static_assert(kSortThreads * 32 / 4 <= kRadix * kSortWarps, "histogram space too small for bank loads");
@@ -227,49 +227,48 @@ __global__ void __launch_bounds__(kSortThreads, 1)
     }
     __syncthreads();
     uint16_t *out = rows + (size_t)blockIdx.x * npad;
+    const int run = npad / 32;  // entries per lane run (see phys_of)
     if constexpr (IPT <= 16) {
         if (L.dual) {
             // With two weight copies, choose per entry which copy the search
-            // gathers from.  One gather instruction of the search kernel reads,
-            // for a 512-entry unit u and a slot j in 0..15, the 32 entries at
-            // u*512 + 16k + j (k = 0..31).  For each such group, greedily put each
-            // entry in the less loaded of its two banks (copy A: i mod 32, copy
-            // B: rot(i) mod 32), then let entries move to a lighter bank.
+            // gathers from.  One gather instruction of the search kernel reads
+            // entry r of every lane run: the 32 entries k * run + r, k = 0..31.
+            // For each such group, greedily put each entry in the less loaded
+            // of its two banks (copy A: i mod 32, copy B: rot(i) mod 32), then
+            // let entries move to a lighter bank.  Bank loads are kept per
+            // thread, bank-major so that the threads do not share banks.
             uint32_t *gchoice = hist + kRadix * kSortWarps;  // one mask per group
-            uint8_t *ld = reinterpret_cast<uint8_t *>(hist) + (size_t)threadIdx.x * 32;
-            const int ngroups = (npad + kUnitElems - 1) / kUnitElems * 16;
-            for (int g = threadIdx.x; g < ngroups; g += kSortThreads) {
+            uint8_t *ld = reinterpret_cast<uint8_t *>(hist) + threadIdx.x;
+            for (int g = threadIdx.x; g < run; g += kSortThreads) {
 #pragma unroll
-                for (int b = 0; b < 32; ++b) ld[b] = 0;
-                const int u = g >> 4, j = g & 15;
+                for (int b = 0; b < 32; ++b) ld[b * kSortThreads] = 0;
                 uint32_t mask = 0;
                 bool pad_seen = false;
                 for (int k = 0; k < 32; ++k) {
-                    const int p = u * kUnitElems + 16 * k + j;
-                    if (p >= npad) break;
+                    const int p = k * run + g;
                     if (p >= n) {
-                        if (!pad_seen) ld[n & 31]++;  // the padding word, read as a broadcast
+                        if (!pad_seen) ld[(n & 31) * kSortThreads]++;  // padding: one broadcast read
                         pad_seen = true;
                         continue;
                     }
                     const int i = sidx[p];
                     const int ba = i & 31, bb = rot_b(i) & 31;
-                    if (ld[bb] < ld[ba]) { ld[bb]++; mask |= 1u << k; }
-                    else ld[ba]++;
+                    if (ld[bb * kSortThreads] < ld[ba * kSortThreads]) { ld[bb * kSortThreads]++; mask |= 1u << k; }
+                    else ld[ba * kSortThreads]++;
                 }
                 // two passes of single moves: an entry leaves its bank when the
                 // other one is at least two entries lighter
                 for (int pass = 0; pass < 2; ++pass)
                     for (int k = 0; k < 32; ++k) {
-                        const int p = u * kUnitElems + 16 * k + j;
-                        if (p >= n || p >= npad) break;
+                        const int p = k * run + g;
+                        if (p >= n) break;
                         const int i = sidx[p];
                         const int ba = i & 31, bb = rot_b(i) & 31;
                         const bool onb = (mask >> k) & 1u;
                         const int cur = onb ? bb : ba, oth = onb ? ba : bb;
-                        if (ld[cur] > ld[oth] + 1) {
-                            ld[cur]--;
-                            ld[oth]++;
+                        if (ld[cur * kSortThreads] > ld[oth * kSortThreads] + 1) {
+                            ld[cur * kSortThreads]--;
+                            ld[oth * kSortThreads]++;
                             mask ^= 1u << k;
                         }
                     }
@@ -281,13 +280,13 @@ __global__ void __launch_bounds__(kSortThreads, 1)
                 if (p < n) {
                     const bool step = (p == n - 1) || (skey[p] < skey[p + 1]);
                     int word = sidx[p];
-                    const int g = (p / kUnitElems) * 16 + (p & 15), k = (p % kUnitElems) >> 4;
+                    const int k = p / run, g = p - k * run;
                     if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
                     e = static_cast<uint16_t>(word | (step ? kFlagBit : 0));
                 } else {
                     e = static_cast<uint16_t>(n);
                 }
-                out[p] = e;
+                out[phys_of(p, run)] = e;
             }
             return;
         }
@@ -300,7 +299,7 @@ __global__ void __launch_bounds__(kSortThreads, 1)
         } else {
             e = static_cast<uint16_t>(n);
         }
-        out[p] = e;
+        out[phys_of(p, run)] = e;
     }
 }
 
@@ -315,12 +314,12 @@ __global__ void k_check_rows(const uint4 *__restrict__ rows, int64_t nvec, Weigh
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvec;
          k += (int64_t)gridDim.x * blockDim.x) {
         const uint4 q = __ldg(rows + k);
-        const int p0 = (int)((k * 8) % npad);
+        const int p0 = (int)((k * 8) % npad);  // physical index of the first entry
         const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
-            const int p = p0 + j;
+            const int p = logical_of(p0 + j, npad / 32);
             const int word = (int)(e & kIndexMask);
             if (p < n) {
                 const bool ok = word < n || (L.dual && word >= L.off_b && word < L.words &&

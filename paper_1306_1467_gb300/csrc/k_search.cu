@@ -13,11 +13,13 @@
 //
 // Three kernels per search:
 //  * k_screen (the hot kernel): streams the whole uint16 table once per round
-//    with TMA, gathers v from shared memory, and forms D with FP32 prefix sums:
-//    each lane sums 16 consecutive entries, a warp scan combines the 32 lane
-//    totals of a 512-entry unit, and the running offset of a row is carried in
-//    double-float (compensated) form.  It writes each feature's FP32 error and
-//    each CTA's minimum.
+//    with TMA, gathers v from shared memory, and forms D with FP32 prefix sums.
+//    A warp scans one row: lane k walks its own run of the value order (the
+//    row layout interleaves 32 runs), summing 16 entries at a time in FP32 and
+//    folding each piece into a compensated (TwoSum) running total; one
+//    double-float warp scan of the 32 run totals per row places every lane's
+//    best prefix in the row.  It writes each feature's FP32 error and each
+//    CTA's minimum.
 //  * k_shortlist: lists every feature whose screened error is within a margin
 //    of the smallest one.
 //  * k_rescan: one CTA per listed feature scans its row again in double-float
@@ -26,11 +28,12 @@
 //    picks the round's stump: lowest error, then feature, split, +1 before -1.
 //
 // Screening error bound (u = 2^-24, sum |v| = T+ + T- = 1 after normalising):
-// a lane's partial sums of 16 terms err by at most 16u times the lane's |v|
-// mass, the 5-level warp scan by 5u times the unit's mass, combining the
-// compensated carry with the unit offset and the lane maximum adds 3u |D|,
-// and forming T+- -/+ D in FP32 adds 2u.  So |screened - exact| <= 26u.  A
-// margin of 64u (twice 32u) keeps every feature that could beat the best one.
+// a piece's partial sums of at most 16 terms err by at most 16u times the
+// piece's |v| mass; the compensated run total and the double-float scan of run
+// totals add O(u^2); placing the piece's extreme on the run total, and that on
+// the run offset, adds 4u |D|; forming T+- -/+ D in FP32 adds 2u.  So
+// |screened - exact| <= 22u.  A margin of 64u (twice 32u) keeps every
+// feature that could beat the best one.
 #include <limits.h>
 #include <math.h>
 
@@ -79,38 +82,33 @@ __device__ __forceinline__ void minmax_if(uint32_t flag, float a, float &mx, flo
         : "r"(flag), "f"(a));
 }
 
-// U consecutive 512-entry units of a stage, worked on together for
-// instruction-level parallelism.  Lane k holds entries 16k .. 16k+15 of each
-// unit.  The stage was written by TMA with the 128-byte swizzle: within each
-// 1 KiB, the 16-byte chunk c of line r sits at chunk c ^ (r & 7), which makes
-// the two 16-byte reads of the 32 lanes bank-conflict free.  Lines at or past
-// `lines_here` read as padding (weight 0, no split).  The arithmetic of each
-// unit, and the order in which units enter the carry, are those of one unit
-// at a time.
-template <int U>
-__device__ __forceinline__ void screen_units(uint32_t sbase, int u0, int lane, int lines_here,
-                                             uint32_t pad2, const float *sv, float &chi,
-                                             float &clo, float &MX, float &MN) {
-    const uint32_t sw = ((uint32_t)lane >> 2) & 7u;
-    const uint32_t c0 = ((2u * ((uint32_t)lane & 3u)) ^ sw) << 4;
-    const uint32_t c1 = ((2u * ((uint32_t)lane & 3u) + 1u) ^ sw) << 4;
-    uint32_t wd[U][8];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const uint32_t line = (uint32_t)(u0 + u) * 8u + ((uint32_t)lane >> 2);
-        uint4 q0 = make_uint4(pad2, pad2, pad2, pad2), q1 = q0;
-        if (line < (uint32_t)lines_here) {
-            q0 = lds128(sbase + line * kLineBytes + c0);
-            q1 = lds128(sbase + line * kLineBytes + c1);
-        }
-        wd[u][0] = q0.x; wd[u][1] = q0.y; wd[u][2] = q0.z; wd[u][3] = q0.w;
-        wd[u][4] = q1.x; wd[u][5] = q1.y; wd[u][6] = q1.z; wd[u][7] = q1.w;
-    }
-    float g[U][16];
+// U pieces of CR chunk rows of a stage (8 entries per lane per chunk row),
+// worked on together for instruction-level parallelism.  Lane k reads chunk
+// t * 32 + k: its own run, in order, 16 bytes at a time, the 32 lanes covering
+// 512 contiguous bytes (no bank conflict).  Each piece is summed in FP32 from
+// zero; its largest and smallest prefix at a valid split, offset by the
+// lane's compensated running total (ahi + alo), update the lane's best
+// (bmx, bmn); then the piece total enters the running total through TwoSum.
+template <int U, int CR>
+__device__ __forceinline__ void scan_pieces(uint32_t sbase, int t0, int lane, const float *sv,
+                                            float &ahi, float &alo, float &bmx, float &bmn) {
+    constexpr int E = CR * kChunkElems;
+    uint32_t wd[U][CR * 4];
 #pragma unroll
     for (int u = 0; u < U; ++u)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int c = 0; c < CR; ++c) {
+            const uint4 q = lds128(sbase + (uint32_t)(((t0 + u * CR + c) * 32 + lane) * 16));
+            wd[u][4 * c + 0] = q.x;
+            wd[u][4 * c + 1] = q.y;
+            wd[u][4 * c + 2] = q.z;
+            wd[u][4 * c + 3] = q.w;
+        }
+    float g[U][E];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < E / 2; ++j) {
             g[u][2 * j] = sv[wd[u][j] & kIndexMask];
             g[u][2 * j + 1] = sv[(wd[u][j] >> 16) & kIndexMask];
         }
@@ -122,42 +120,28 @@ __device__ __forceinline__ void screen_units(uint32_t sbase, int u0, int lane, i
         mn[u] = INFINITY;
     }
 #pragma unroll
-    for (int j = 0; j < 16; ++j)
+    for (int j = 0; j < E; ++j)
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             a[u] += g[u][j];
             const uint32_t fl = (j & 1) ? (wd[u][j >> 1] & 0x80000000u) : (wd[u][j >> 1] & 0x8000u);
             minmax_if(fl, a[u], mx[u], mn[u]);
         }
-    float x[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) x[u] = a[u];
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1)
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const float y = __shfl_up_sync(0xffffffffu, x[u], d);
-            if (lane >= d) x[u] += y;
-        }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        float excl = __shfl_up_sync(0xffffffffu, x[u], 1);
-        if (lane == 0) excl = 0.f;
-        const float tot = __shfl_sync(0xffffffffu, x[u], 31);
-        const float base = chi + (clo + excl);
-        MX = fmaxf(MX, base + mx[u]);
-        MN = fminf(MN, base + mn[u]);
-        float s, e;
-        two_sum(chi, tot, s, e);
-        chi = s;
-        clo += e;
+        bmx = fmaxf(bmx, ahi + (alo + mx[u]));
+        bmn = fminf(bmn, ahi + (alo + mn[u]));
+        float sum, err;
+        two_sum(ahi, a[u], sum, err);
+        ahi = sum;
+        alo += err;
     }
 }
 
 template <int U>
 __global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
     k_screen(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ v, int words,
-             int pad_word, int lines_per_row, int box_lines, int stage_lines, int64_t nfeat,
+             int lines_per_row, int box_lines, int stage_lines, int64_t nfeat,
              int stages, RoundState *rs, float *__restrict__ ferr, float *__restrict__ bmin) {
     if (rs->status != VJB_OK) return;
     extern __shared__ __align__(16) float sv[];  // weights at the base of dynamic shared memory
@@ -201,13 +185,12 @@ __global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
     __syncwarp();
 
     const float Tp = (float)rs->t_pos, Tm = (float)rs->t_neg;
-    const uint32_t pad2 = (uint32_t)pad_word | ((uint32_t)pad_word << 16);
     float best = INFINITY;
     int64_t seq = 0;
     bool ok = true;
     for (int64_t k = 0; k < nf_w && ok; ++k) {
         const int64_t f = gw + k * G;
-        float chi = 0.f, clo = 0.f, MX = 0.f, MN = 0.f;  // D(0) = 0 is a valid split
+        float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
         for (int c = 0; c < nc; ++c) {
             const int stage = (int)(seq % stages);
             const uint32_t par = (uint32_t)((seq / stages) & 1);
@@ -216,14 +199,15 @@ __global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
                 break;
             }
             const int lines_here = min(box_lines, lines_per_row - c * box_lines);
+            const int crs = lines_here >> 2;  // chunk rows (a line is a quarter of one)
             const uint32_t sbase = ring_w + (uint32_t)stage * stage_bytes;
-            if (lines_here == box_lines && (box_lines & (8 * U - 1)) == 0) {
-                for (int u0 = 0; u0 < box_lines / 8; u0 += U)
-                    screen_units<U>(sbase, u0, lane, box_lines, pad2, sv, chi, clo, MX, MN);
+            if (crs == 8) {
+#pragma unroll
+                for (int t = 0; t < 8; t += 2 * U) scan_pieces<U, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
             } else {
-                const int units = (lines_here + 7) >> 3;
-                for (int u0 = 0; u0 < units; u0 += U)
-                    screen_units<U>(sbase, u0, lane, lines_here, pad2, sv, chi, clo, MX, MN);
+                int t = 0;
+                for (; t + 2 <= crs; t += 2) scan_pieces<1, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+                if (t < crs) scan_pieces<1, 1>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
             }
             __syncwarp();
             if (lane == 0 && seq + stages < total) {
@@ -233,8 +217,19 @@ __global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
             ++seq;
         }
         if (!ok) break;
-        MX = warp_max(MX);
-        MN = warp_min(MN);
+        // the runs of the lanes below come first: exclusive scan of the run totals
+        DF x{ahi, alo};
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const DF y = df_shfl_up(x, d);
+            if (lane >= d) x = df_add(y, x);
+        }
+        DF excl = df_shfl_up(x, 1);
+        if (lane == 0) excl = DF{0.f, 0.f};
+        float MX = warp_max(excl.hi + (excl.lo + bmx));
+        float MN = warp_min(excl.hi + (excl.lo + bmn));
+        MX = fmaxf(MX, 0.f);  // split 0: D = 0
+        MN = fminf(MN, 0.f);
         const float e = fminf(Tp - MX, Tm + MN);
         if (lane == 0) {
             ferr[f] = e;
@@ -268,15 +263,15 @@ cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, const WeightL
     const int threads = shape.warps * 32;
     switch (shape.unroll) {
     case 1:
-        k_screen<1><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines,
+        k_screen<1><<<grid, threads, sm, st>>>(*tmap, v, L.words, lines_per_row, box_lines,
                                                shape.box_lines, nfeat, shape.stages, rs, ferr, bmin);
         break;
     case 4:
-        k_screen<4><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines,
+        k_screen<4><<<grid, threads, sm, st>>>(*tmap, v, L.words, lines_per_row, box_lines,
                                                shape.box_lines, nfeat, shape.stages, rs, ferr, bmin);
         break;
     default:
-        k_screen<2><<<grid, threads, sm, st>>>(*tmap, v, L.words, L.n, lines_per_row, box_lines,
+        k_screen<2><<<grid, threads, sm, st>>>(*tmap, v, L.words, lines_per_row, box_lines,
                                                shape.box_lines, nfeat, shape.stages, rs, ferr, bmin);
     }
     return cudaGetLastError();
@@ -364,46 +359,41 @@ __device__ __forceinline__ Candidate cand_shfl_xor(const Candidate &c, int d) {
 
 constexpr int kRescanWarps = 8;
 
-struct SliceResult {
+struct RunResult {
     DF total, mx, mn;
     int smx, smn;
 };
 
-// One warp scans units [ua, ub) of a row in double-float; returns (lane 0) the
-// slice total and its largest / smallest prefix at a valid split, relative to
-// the slice start, with the lowest position on ties (INT_MAX if none).
-__device__ SliceResult rescan_slice(const uint16_t *__restrict__ row, int npad, int ua, int ub,
-                                    const float *__restrict__ v, uint32_t pad2, int lane) {
+// One warp scans lane run k of a row in double-float: 32 chunks of 8 entries
+// at a time, lane i holding chunk u0 + i of the run.  Returns (in every lane)
+// the run total and its largest / smallest prefix at a valid split, relative
+// to the run start, with the split position (number of entries before it in
+// the whole value order) and the lowest position on ties (INT_MAX if none).
+__device__ RunResult rescan_run(const uint16_t *__restrict__ row, int run, int k,
+                                const float *__restrict__ v, int lane) {
     DF carry{0.f, 0.f}, bmax{-INFINITY, 0.f}, bmn{INFINITY, 0.f};
     int smax = INT_MAX, smn = INT_MAX;
-    for (int u = ua; u < ub; ++u) {
-        const int off = u * kUnitElems + lane * 16;
-        uint32_t wd[8];
-        if (off < npad) {
-            const uint4 *p = reinterpret_cast<const uint4 *>(row + off);
-            const uint4 a = __ldg(p), b = __ldg(p + 1);
-            wd[0] = a.x; wd[1] = a.y; wd[2] = a.z; wd[3] = a.w;
-            wd[4] = b.x; wd[5] = b.y; wd[6] = b.z; wd[7] = b.w;
-        } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) wd[j] = pad2;
-        }
-        float g[16];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            g[2 * j] = __ldg(v + (wd[j] & kIndexMask));
-            g[2 * j + 1] = __ldg(v + ((wd[j] >> 16) & kIndexMask));
+    const int nch = run / kChunkElems;
+    for (int u0 = 0; u0 < nch; u0 += 32) {
+        const int t = u0 + lane;
+        uint32_t wd[4] = {0u, 0u, 0u, 0u};
+        const bool have = t < nch;
+        if (have) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row + (size_t)(t * 32 + k) * kChunkElems));
+            wd[0] = q.x; wd[1] = q.y; wd[2] = q.z; wd[3] = q.w;
         }
         DF a{0.f, 0.f}, lmx{-INFINITY, 0.f}, lmn{INFINITY, 0.f};
         int lsx = INT_MAX, lsn = INT_MAX;
+        if (have) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            a = df_add_f(a, g[j]);
-            const uint32_t fl = (j & 1) ? (wd[j >> 1] & 0x80000000u) : (wd[j >> 1] & 0x8000u);
-            if (fl) {
-                const int pos = off + j + 1;
-                if (df_less(lmx, a)) { lmx = a; lsx = pos; }
-                if (df_less(a, lmn)) { lmn = a; lsn = pos; }
+            for (int j = 0; j < kChunkElems; ++j) {
+                const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
+                a = df_add_f(a, __ldg(v + (e & kIndexMask)));
+                if (e & kFlagBit) {
+                    const int pos = k * run + t * kChunkElems + j + 1;
+                    if (df_less(lmx, a)) { lmx = a; lsx = pos; }
+                    if (df_less(a, lmn)) { lmn = a; lsn = pos; }
+                }
             }
         }
         DF x = a;
@@ -435,7 +425,7 @@ __device__ SliceResult rescan_slice(const uint16_t *__restrict__ row, int npad, 
         const int on_s = __shfl_xor_sync(0xffffffffu, smn, d);
         if (df_less(on, bmn) || (df_eq(on, bmn) && on_s < smn)) { bmn = on; smn = on_s; }
     }
-    SliceResult r;
+    RunResult r;
     r.total = carry;
     r.mx = bmax;
     r.mn = bmn;
@@ -445,29 +435,29 @@ __device__ SliceResult rescan_slice(const uint16_t *__restrict__ row, int npad, 
 }
 
 __global__ void __launch_bounds__(kRescanWarps * 32)
-    k_rescan(const uint16_t *__restrict__ rows, int npad, const float *__restrict__ v, int pad_word,
+    k_rescan(const uint16_t *__restrict__ rows, int npad, const float *__restrict__ v,
              RoundState *rs, const int32_t *__restrict__ cand_ids, Candidate *__restrict__ cands) {
     if (rs->status != VJB_OK || rs->forced) return;
-    __shared__ SliceResult sres[kRescanWarps];
+    __shared__ RunResult rres[32];
     __shared__ Candidate wc[kRescanWarps];
     __shared__ bool last_cta;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int cnt = rs->cand_count;
-    const int units = (npad + kUnitElems - 1) / kUnitElems;
-    const uint32_t pad2 = (uint32_t)pad_word | ((uint32_t)pad_word << 16);
+    const int run = npad / 32;
     const DF Tp = df_from_double(rs->t_pos), Tm = df_from_double(rs->t_neg);
     for (int c = blockIdx.x; c < cnt; c += gridDim.x) {
         const int32_t f = cand_ids[c];
         const uint16_t *row = rows + (size_t)f * npad;
-        const int ua = units * warp / kRescanWarps, ub = units * (warp + 1) / kRescanWarps;
-        const SliceResult r = rescan_slice(row, npad, ua, ub, v, pad2, lane);
-        if (lane == 0) sres[warp] = r;
+        for (int k = warp; k < 32; k += kRescanWarps) {
+            const RunResult r = rescan_run(row, run, k, v, lane);
+            if (lane == 0) rres[k] = r;
+        }
         __syncthreads();
         if (threadIdx.x == 0) {
             DF offs{0.f, 0.f}, bmax{0.f, 0.f}, bmn{0.f, 0.f};  // split 0: D = 0
             int smax = 0, smn = 0;
-            for (int w = 0; w < kRescanWarps; ++w) {
-                const SliceResult &q = sres[w];
+            for (int k = 0; k < 32; ++k) {  // runs in value order
+                const RunResult &q = rres[k];
                 if (q.smx != INT_MAX) {
                     const DF cc = df_add(offs, q.mx);
                     if (df_less(bmax, cc)) { bmax = cc; smax = q.smx; }
@@ -534,7 +524,8 @@ __global__ void __launch_bounds__(kRescanWarps * 32)
 cudaError_t launch_rescan(const uint16_t *rows, int npad, const float *v, const WeightLayout &L,
                           RoundState *rs, const int32_t *cand_ids, Candidate *cands, int grid,
                           cudaStream_t st) {
-    k_rescan<<<grid, kRescanWarps * 32, 0, st>>>(rows, npad, v, L.n, rs, cand_ids, cands);
+    (void)L;
+    k_rescan<<<grid, kRescanWarps * 32, 0, st>>>(rows, npad, v, rs, cand_ids, cands);
     return cudaGetLastError();
 }
 

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(kUpdateThreads)
         bool h;
         if (!forced) {
             // sorted position k: the first s positions are "below" the threshold
-            i = word_to_sample(rows[(size_t)f * npad + k] & kIndexMask, L);
+            i = word_to_sample(rows[(size_t)f * npad + phys_of(k, npad / 32)] & kIndexMask, L);
             const bool bl = k < s;
             h = (p > 0) ? bl : !bl;
         } else {
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kUpdateThreads)
         // p=-1 -> value at position s-1 (min-1 at s = 0)
         const uint16_t *row = rows + (size_t)f * npad;
         auto val_at = [&](int pos) {
-            const int i = word_to_sample(row[pos] & kIndexMask, L);
+            const int i = word_to_sample(row[phys_of(pos, npad / 32)] & kIndexMask, L);
             return haar_value(ii_t, ii_stride, w, d.type, d.x, d.y, d.w, d.h, i);
         };
         if (p > 0) theta = (s < n) ? val_at(s) : val_at(n - 1) + 1;

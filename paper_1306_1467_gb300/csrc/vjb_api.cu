@@ -173,7 +173,7 @@ int make_tensor_map(vjb_ctx *c) {
     cuuint32_t box[3] = {(cuuint32_t)kLineElems, (cuuint32_t)c->box_lines, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = encode(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, c->d_rows, dims, strides, box,
-                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return fail(VJB_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     c->tmap_ok = true;
@@ -440,7 +440,7 @@ int prepare_tables(vjb_ctx *c) {
         }
         CK(cudaMalloc(&c->d_feat, sizeof(DevFeature) * df.size()));
         CK(cudaMemcpy(c->d_feat, df.data(), sizeof(DevFeature) * df.size(), cudaMemcpyHostToDevice));
-        c->npad = (c->n + kLineElems - 1) / kLineElems * kLineElems;
+        c->npad = (c->n + kRowAlign - 1) / kRowAlign * kRowAlign;
         c->lines = c->npad / kLineElems;
         c->box_lines = 0;  // set with the search shape
     }
@@ -789,19 +789,17 @@ int vjb_sorted_rows(vjb_ctx *c, int64_t f0, int64_t nf, uint16_t *out) {
     if (nf == 0) return VJB_OK;
     int rc = set_dev(c);
     if (rc) return rc;
-    CK(cudaMemcpy2DAsync(out, sizeof(uint16_t) * c->n, c->d_rows + (size_t)f0 * c->npad,
-                         sizeof(uint16_t) * c->npad, sizeof(uint16_t) * c->n, (size_t)nf,
-                         cudaMemcpyDeviceToHost, c->stream));
+    // rows in value order: undo the lane-run interleave and name samples, not weight words
+    std::vector<uint16_t> raw((size_t)nf * c->npad);
+    CK(cudaMemcpyAsync(raw.data(), c->d_rows + (size_t)f0 * c->npad, sizeof(uint16_t) * raw.size(),
+                       cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
-    // the device table names samples through words of the weight array
-    if (c->lay.dual) {
-        const size_t cnt = (size_t)nf * c->n;
-        for (size_t k = 0; k < cnt; ++k) {
-            const uint16_t e = out[k];
-            const int word = e & kIndexMask;
-            out[k] = (uint16_t)((e & kFlagBit) | word_to_sample(word, c->lay));
+    const int run = c->npad / 32;
+    for (int64_t r = 0; r < nf; ++r)
+        for (int e = 0; e < c->n; ++e) {
+            const uint16_t x = raw[(size_t)r * c->npad + phys_of(e, run)];
+            out[(size_t)r * c->n + e] = (uint16_t)((x & kFlagBit) | word_to_sample(x & kIndexMask, c->lay));
         }
-    }
     return VJB_OK;
 }
 

@@ -83,6 +83,24 @@ constexpr int kLineBytes = 128;
 constexpr int kBoxLinesMax = 32;
 constexpr int kStageBytes = kBoxLinesMax * kLineBytes;  // 4096
 constexpr int kUnitElems = 512;                         // 32 lanes x 16 entries
+
+// Row layout of the sorted table.  A row holds npad entries (n rounded up to
+// a multiple of 256; entries from n on are padding).  The value order is cut
+// into 32 runs of npad / 32 entries, one per lane of the warp that scans the
+// row, and the runs are interleaved in 16-byte chunks of 8 entries: chunk t of
+// run k is chunk t * 32 + k of the row.  A 512-byte "chunk row" thus holds the
+// next 8 entries of every run, and a lane reading chunk t * 32 + lane walks its
+// own run in order.
+constexpr int kRowAlign = 256;
+constexpr int kChunkElems = 8;
+__host__ __device__ __forceinline__ int phys_of(int e, int run) {
+    const int k = e / run, r = e - k * run;
+    return ((r >> 3) * 32 + k) * kChunkElems + (r & 7);
+}
+__host__ __device__ __forceinline__ int logical_of(int phys, int run) {
+    const int c = phys >> 3;
+    return (c & 31) * run + (c >> 5) * kChunkElems + (phys & 7);
+}
 constexpr uint16_t kFlagBit = 0x8000u;
 constexpr uint16_t kIndexMask = 0x7FFFu;
 

@@ -7,8 +7,9 @@ a trained context's sorted table and weights with torch (the test may
 allocate; the entry point must not), calls the entry point through the C ABI
 twice in a row -- each time on the weights of the next round -- and compares
 its per-feature errors and its best feature with the library's own search of
-that round (vjb_train_round, read back with vjb_screen_errors), within the
-screening tolerance the other GPU tests use.
+that round (vjb_train_round, read back with vjb_screen_errors).  Each search
+is within the screening tolerance of the other GPU tests of the exact errors,
+so the two agree within twice that tolerance.
 
 The file is named so that pytest collects it last.
 """
@@ -21,6 +22,8 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 SCREEN_TOL = 32 * 2.0 ** -24  # the screening bound used by the parity tests
+# both searches lie within SCREEN_TOL of the exact errors, summed in different orders
+PAIR_TOL = 2 * SCREEN_TOL
 
 
 def test_noalloc_search_matches_library_search():
@@ -59,10 +62,10 @@ def test_noalloc_search_matches_library_search():
             st, _ = tr.train_round()
             assert st == vjb.OK
             ref = tr.screen_errors()
-            assert np.max(np.abs(got.astype(np.float64) - ref)) <= SCREEN_TOL, call
+            assert np.max(np.abs(got.astype(np.float64) - ref)) <= PAIR_TOL, call
             bf = int(best_f.item())
             assert bf == int(np.argmin(got)), call
-            assert abs(float(best_e.item()) - float(tr.info()["screen_min"])) <= SCREEN_TOL, call
+            assert abs(float(best_e.item()) - float(tr.info()["screen_min"])) <= PAIR_TOL, call
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
