@@ -59,29 +59,53 @@ cudaError_t launch_feature_values(const int32_t *ii_t, int ii_stride, int n, int
 }
 
 // ---- K3: segmented stable sort ---------------------------------------------------------
-// One 1024-thread CTA per feature row.  Keys are value - min (so they are
-// non-negative), sorted by an LSD radix sort with 8-bit digits over only the
-// bits the row's value span needs.  Each pass ranks digits stably: items are
-// held in registers in a "warp-striped" layout (warp wp, column j, lane l ->
-// position wp*32*IPT + j*32 + l), a warp walks its columns in position order
-// and ranks equal digits inside a column with __match_any_sync, and the
+// One 1024-thread CTA per feature row.  The CTA first evaluates its feature on
+// every window (the K2 arithmetic, fused here so the int32 values never leave
+// the SM), then sorts keys value - min (non-negative) by an LSD radix sort with
+// 8-bit digits over only the bits the row's value span needs.  Each pass ranks
+// digits stably: items are held in registers in a "warp-striped" layout (warp
+// wp, column j, lane l -> position wp*32*IPT + j*32 + l), a warp walks its
+// columns in position order and ranks equal digits inside a column, and the
 // per-(digit, warp) counts are scanned digit-major.  Equal keys therefore keep
 // their order, and since items start in sample order, ties end up ordered by
-// sample index.  Output entry = sample index | (value < next value) << 15;
-// positions n .. npad-1 hold the padding entry n (weight 0, no flag).
+// sample index.  Output entry = weight word | (value < next value) << 15,
+// written in the lane-run row layout; positions n .. npad-1 hold the padding
+// word n (weight 0, no flag).
 constexpr int kSortThreads = 1024;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kRadix = 256;
+constexpr int kHistStride = kSortWarps + 1;  // (digit, warp) counters, padded against bank conflicts
+constexpr int kHistWords = kRadix * kHistStride;
 // Gather groups of a row with two weight copies (n <= 16352): one per entry
 // of a lane run, at most 16384 / 32.  Their masks sit after the histogram and
 // the per-thread bank loads (32 bytes each) reuse the histogram space.
 constexpr int kMaxGroups = 512;
-static_assert(kSortThreads * 32 / 4 <= kRadix * kSortWarps, "histogram space too small for bank loads");
+static_assert(kSortThreads * 32 / 4 <= kHistWords, "histogram space too small for bank loads");
+
+#ifndef VJB_SORT_BALLOT
+#define VJB_SORT_BALLOT 0
+#endif
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
     uint32_t m;
     asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
     return m;
+}
+
+// Lanes of the warp holding the same 8-bit digit as this lane.
+__device__ __forceinline__ uint32_t same_digit(uint32_t d) {
+#if VJB_SORT_BALLOT
+    uint32_t eq = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const uint32_t bit = (d >> b) & 1u;
+        const uint32_t m = __ballot_sync(0xffffffffu, bit);
+        eq &= bit ? m : ~m;
+    }
+    return eq;
+#else
+    return __match_any_sync(0xffffffffu, d);
+#endif
 }
 
 // Exclusive scan of one int per thread over the CTA; returns the thread's
@@ -114,38 +138,42 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t *w
 
 template <int IPT>
 __global__ void __launch_bounds__(kSortThreads, 1)
-    k_sort_rows(const int32_t *__restrict__ vals, WeightLayout L, uint16_t *__restrict__ rows, int npad) {
+    k_sort_rows(const int32_t *__restrict__ ii_t, int ii_stride, int w,
+                const DevFeature *__restrict__ feat, int64_t f0, WeightLayout L,
+                uint16_t *__restrict__ rows, int npad) {
     constexpr int NP = kSortThreads * IPT;
     const int n = L.n;
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *skey = reinterpret_cast<uint32_t *>(smem);
-    uint32_t *hist = skey + NP;                    // kRadix * kSortWarps (+ kMaxGroups)
-    uint32_t *ws = hist + kRadix * kSortWarps + (IPT <= 16 ? kMaxGroups : 0);  // kSortWarps
-    int32_t *mm = reinterpret_cast<int32_t *>(ws + kSortWarps);  // 2
-    uint16_t *sidx = reinterpret_cast<uint16_t *>(mm + 2);       // NP
+    uint32_t *hist = skey + NP;                                            // kHistWords (+ kMaxGroups)
+    uint32_t *ws = hist + kHistWords + (IPT <= 16 ? kMaxGroups : 0);        // kSortWarps
+    int32_t *mm = reinterpret_cast<int32_t *>(ws + kSortWarps);             // 2
+    uint16_t *sidx = reinterpret_cast<uint16_t *>(mm + 2);                  // NP
 
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    const int32_t *vr = vals + (size_t)blockIdx.x * n;
     const int pos0 = wp * 32 * IPT + lane;
+    const DevFeature d = feat[f0 + blockIdx.x];
 
+    // the feature on every window, into shared memory (K2's arithmetic)
+    int32_t lo = INT_MAX, hi = INT_MIN;
+    for (int p = threadIdx.x; p < n; p += kSortThreads) {
+        const int32_t x = haar_value(ii_t, ii_stride, w, d.type, d.x, d.y, d.w, d.h, p);
+        skey[p] = static_cast<uint32_t>(x);
+        lo = min(lo, x);
+        hi = max(hi, x);
+    }
+    __syncthreads();
     uint32_t key[IPT];
     uint32_t ipk[(IPT + 1) / 2];  // two 16-bit sample indices per register
-    int32_t lo = INT_MAX, hi = INT_MIN;
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const int p = pos0 + j * 32;
-        int32_t x = 0;
-        if (p < n) {
-            x = vr[p];
-            lo = min(lo, x);
-            hi = max(hi, x);
-        }
-        key[j] = static_cast<uint32_t>(x);
+        key[j] = p < n ? skey[p] : 0u;
     }
 #pragma unroll
-    for (int d = 16; d; d >>= 1) {
-        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, d));
-        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, d));
+    for (int s = 16; s; s >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, s));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, s));
     }
     if (threadIdx.x == 0) { mm[0] = INT_MAX; mm[1] = INT_MIN; }
     __syncthreads();
@@ -166,14 +194,14 @@ __global__ void __launch_bounds__(kSortThreads, 1)
 
     const uint32_t lt = lanemask_lt();
     for (int shift = 0; shift < bits; shift += 8) {
-        for (int k = threadIdx.x; k < kRadix * kSortWarps; k += kSortThreads) hist[k] = 0;
+        for (int k = threadIdx.x; k < kHistWords; k += kSortThreads) hist[k] = 0;
         __syncthreads();
         // count digits per (digit, warp)
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
-            const uint32_t d = (key[j] >> shift) & (kRadix - 1);
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (lane == __ffs(peers) - 1) atomicAdd(&hist[d * kSortWarps + wp], __popc(peers));
+            const uint32_t dg = (key[j] >> shift) & (kRadix - 1);
+            const uint32_t peers = same_digit(dg);
+            if (lane == __ffs(peers) - 1) hist[dg * kHistStride + wp] += __popc(peers);
         }
         __syncthreads();
         // exclusive scan, digit-major then warp: thread t owns 8 consecutive counters
@@ -183,13 +211,15 @@ __global__ void __launch_bounds__(kSortThreads, 1)
             uint32_t s = 0;
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
-                c[q] = hist[threadIdx.x * PER + q];
+                const int lin = threadIdx.x * PER + q;
+                c[q] = hist[(lin >> 5) * kHistStride + (lin & 31)];
                 s += c[q];
             }
             uint32_t off = block_exclusive_scan(s, ws);
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
-                hist[threadIdx.x * PER + q] = off;
+                const int lin = threadIdx.x * PER + q;
+                hist[(lin >> 5) * kHistStride + (lin & 31)] = off;
                 off += c[q];
             }
         }
@@ -197,11 +227,11 @@ __global__ void __launch_bounds__(kSortThreads, 1)
         // scatter in position order
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
-            const uint32_t d = (key[j] >> shift) & (kRadix - 1);
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const uint32_t base = hist[d * kSortWarps + wp];
+            const uint32_t dg = (key[j] >> shift) & (kRadix - 1);
+            const uint32_t peers = same_digit(dg);
+            const uint32_t base = hist[dg * kHistStride + wp];
             __syncwarp();
-            if (lane == __ffs(peers) - 1) hist[d * kSortWarps + wp] = base + __popc(peers);
+            if (lane == __ffs(peers) - 1) hist[dg * kHistStride + wp] = base + __popc(peers);
             __syncwarp();
             const uint32_t dst = base + __popc(peers & lt);
             skey[dst] = key[j];
@@ -275,23 +305,25 @@ __global__ void __launch_bounds__(kSortThreads, 1)
                 gchoice[g] = mask;
             }
             __syncthreads();
-            for (int p = threadIdx.x; p < npad; p += kSortThreads) {
+            for (int P = threadIdx.x; P < npad; P += kSortThreads) {
+                const int p = logical_of(P, run);
                 uint16_t e;
                 if (p < n) {
                     const bool step = (p == n - 1) || (skey[p] < skey[p + 1]);
                     int word = sidx[p];
-                    const int k = p / run, g = p - k * run;
+                    const int k = (P >> 3) & 31, g = (P >> 8) * kChunkElems + (P & 7);  // p = k * run + g
                     if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
                     e = static_cast<uint16_t>(word | (step ? kFlagBit : 0));
                 } else {
                     e = static_cast<uint16_t>(n);
                 }
-                out[phys_of(p, run)] = e;
+                out[P] = e;
             }
             return;
         }
     }
-    for (int p = threadIdx.x; p < npad; p += kSortThreads) {
+    for (int P = threadIdx.x; P < npad; P += kSortThreads) {
+        const int p = logical_of(P, run);
         uint16_t e;
         if (p < n) {
             const bool step = (p == n - 1) || (skey[p] < skey[p + 1]);
@@ -299,34 +331,37 @@ __global__ void __launch_bounds__(kSortThreads, 1)
         } else {
             e = static_cast<uint16_t>(n);
         }
-        out[phys_of(p, run)] = e;
+        out[P] = e;
     }
 }
 
 // Validation of a finished table: every entry before position n names a
 // sample below n through a word of the weight array, every entry from n on is
 // the padding word n.  Sets kFlagBadTable in `flags` otherwise.  The search
-// kernels rely on this to gather weights without bounds checks.
-__global__ void k_check_rows(const uint4 *__restrict__ rows, int64_t nvec, WeightLayout L, int npad,
-                             int32_t *flags) {
+// kernels rely on this to gather weights without bounds checks.  One CTA per
+// row at a time, one 16-byte chunk (8 entries) per thread.
+__global__ void k_check_rows(const uint16_t *__restrict__ rows, int64_t nfeat, WeightLayout L,
+                             int npad, int32_t *flags) {
     bool bad = false;
-    const int n = L.n;
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nvec;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        const uint4 q = __ldg(rows + k);
-        const int p0 = (int)((k * 8) % npad);  // physical index of the first entry
-        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+    const int n = L.n, run = npad / 32, nch = npad / kChunkElems;
+    for (int64_t f = blockIdx.x; f < nfeat; f += gridDim.x) {
+        const uint4 *row = reinterpret_cast<const uint4 *>(rows + (size_t)f * npad);
+        for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+            const uint4 q = __ldg(row + c);
+            const int p0 = (c & 31) * run + (c >> 5) * kChunkElems;  // logical position of entry 0
+            const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
-            const int p = logical_of(p0 + j, npad / 32);
-            const int word = (int)(e & kIndexMask);
-            if (p < n) {
-                const bool ok = word < n || (L.dual && word >= L.off_b && word < L.words &&
-                                             unrot_b(word - L.off_b) < n);
-                bad |= !ok;
-            } else {
-                bad |= e != (uint32_t)n;
+            for (int j = 0; j < 8; ++j) {
+                const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
+                const int p = p0 + j;
+                const int word = (int)(e & kIndexMask);
+                if (p < n) {
+                    const bool ok = word < n || (L.dual && word >= L.off_b && word < L.words &&
+                                                 unrot_b(word - L.off_b) < n);
+                    bad |= !ok;
+                } else {
+                    bad |= e != (uint32_t)n;
+                }
             }
         }
     }
@@ -335,41 +370,277 @@ __global__ void k_check_rows(const uint4 *__restrict__ rows, int64_t nvec, Weigh
 
 cudaError_t launch_check_rows(const uint16_t *rows, int64_t nfeat, const WeightLayout &L, int npad,
                               int32_t *flags, int grid, cudaStream_t st) {
-    const int64_t nvec = nfeat * (int64_t)npad / 8;
-    k_check_rows<<<grid, 256, 0, st>>>(reinterpret_cast<const uint4 *>(rows), nvec, L, npad, flags);
+    k_check_rows<<<grid, 256, 0, st>>>(rows, nfeat, L, npad, flags);
     return cudaGetLastError();
 }
 
 template <int IPT>
 static size_t sort_smem() {
-    const size_t hist_words = kRadix * kSortWarps + (IPT <= 16 ? kMaxGroups : 0);
+    const size_t hist_words = kHistWords + (IPT <= 16 ? kMaxGroups : 0);
     return (size_t)kSortThreads * IPT * 4 + hist_words * 4 + kSortWarps * 4 + 8 +
            (size_t)kSortThreads * IPT * 2;
 }
 
 template <int IPT>
-static cudaError_t launch_sort_ipt(const int32_t *vals, const WeightLayout &L, int64_t nf,
-                                   uint16_t *rows, int npad, cudaStream_t st) {
+static cudaError_t launch_sort_ipt(const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
+                                   int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows,
+                                   int npad, cudaStream_t st) {
     const size_t sm = sort_smem<IPT>();
     cudaError_t e = cudaFuncSetAttribute(k_sort_rows<IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
-    k_sort_rows<IPT><<<(unsigned)nf, kSortThreads, sm, st>>>(vals, L, rows, npad);
+    k_sort_rows<IPT><<<(unsigned)nf, kSortThreads, sm, st>>>(ii_t, ii_stride, w, feat, f0, L, rows, npad);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort_rows(const int32_t *vals, const WeightLayout &L, int64_t nf, uint16_t *rows,
-                             int npad, cudaStream_t st) {
+// ---- K3, packed variant ----------------------------------------------------------------
+// The same stable sort for rows whose items fit one 32-bit word: value - min
+// in the high bits above a sample index of ib bits.  That holds when
+// n <= 16384 (ib <= 14) and a value span below 2^18 (every window of at most
+// 1028 pixels, 255 * w * h < 2^18).  Items move as one word, the radix digit
+// has 9 bits (two passes cover an 18-bit span), and a CTA of 512 threads
+// needs about 100 KiB of shared memory, so two rows sort per SM at a time.
+// Only the value bits are sorted; the starting index order and stable passes
+// order ties by sample index.
+constexpr int kPkThreads = 512;
+constexpr int kPkWarps = kPkThreads / 32;
+constexpr int kPkDigitBits = 9;
+constexpr int kPkRadix = 1 << kPkDigitBits;
+constexpr int kPkHistStride = kPkWarps + 1;
+constexpr int kPkHistWords = kPkRadix * kPkHistStride;
+static_assert(kPkThreads * 32 / 4 <= kPkHistWords, "histogram space too small for bank loads");
+
+template <int IPT>
+__global__ void __launch_bounds__(kPkThreads, 2)
+    k_sort_rows_packed(const int32_t *__restrict__ ii_t, int ii_stride, int w,
+                       const DevFeature *__restrict__ feat, int64_t f0, WeightLayout L,
+                       uint16_t *__restrict__ rows, int npad, int32_t *flags) {
+    constexpr int NP = kPkThreads * IPT;
+    const int n = L.n;
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t *skey = reinterpret_cast<uint32_t *>(smem);            // NP items
+    uint32_t *hist = skey + NP;                                     // kPkHistWords
+    uint32_t *gchoice = hist + kPkHistWords;                        // kMaxGroups
+    uint32_t *ws = gchoice + kMaxGroups;                            // kPkWarps
+    int32_t *mm = reinterpret_cast<int32_t *>(ws + kPkWarps);       // 2
+
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int pos0 = wp * 32 * IPT + lane;
+    const DevFeature d = feat[f0 + blockIdx.x];
+
+    // the feature on every window (K2's arithmetic)
+    int32_t lo = INT_MAX, hi = INT_MIN;
+    for (int p = threadIdx.x; p < n; p += kPkThreads) {
+        const int32_t x = haar_value(ii_t, ii_stride, w, d.type, d.x, d.y, d.w, d.h, p);
+        skey[p] = static_cast<uint32_t>(x);
+        lo = min(lo, x);
+        hi = max(hi, x);
+    }
+#pragma unroll
+    for (int s = 16; s; s >>= 1) {
+        lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, s));
+        hi = max(hi, __shfl_xor_sync(0xffffffffu, hi, s));
+    }
+    if (threadIdx.x == 0) { mm[0] = INT_MAX; mm[1] = INT_MIN; }
+    __syncthreads();
+    if (lane == 0) { atomicMin(&mm[0], lo); atomicMax(&mm[1], hi); }
+    __syncthreads();
+    lo = mm[0];
+    hi = mm[1];
+    const uint32_t span = static_cast<uint32_t>(hi) - static_cast<uint32_t>(lo);
+    const int bits = span ? 32 - __clz(span) : 0;
+    const int ib = 32 - __clz((uint32_t)(n - 1));  // bits of a sample index
+    const uint32_t imask = (1u << ib) - 1u;
+    if (bits + ib > 32) {  // the host's size check rules this out; never pack silently wrong
+        if (threadIdx.x == 0) atomicOr(flags, kFlagBadTable);
+        return;
+    }
+    uint32_t c[IPT];
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int p = pos0 + j * 32;
+        // padding items take the all-ones word: they sort after every real item
+        c[j] = (p < n) ? (((skey[p] - static_cast<uint32_t>(lo)) << ib) | (uint32_t)p) : 0xffffffffu;
+    }
+    __syncthreads();
+
+    const uint32_t lt = lanemask_lt();
+    for (int shift = 0; shift < bits; shift += kPkDigitBits) {
+        const int sh = ib + shift;
+        for (int k = threadIdx.x; k < kPkHistWords; k += kPkThreads) hist[k] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const uint32_t dg = (c[j] >> sh) & (kPkRadix - 1);
+            const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            if (lane == __ffs(peers) - 1) hist[dg * kPkHistStride + wp] += __popc(peers);
+        }
+        __syncthreads();
+        {
+            constexpr int PER = kPkRadix * kPkWarps / kPkThreads;  // 16
+            uint32_t cnt[PER];
+            uint32_t s = 0;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int lin = threadIdx.x * PER + q;
+                cnt[q] = hist[(lin / kPkWarps) * kPkHistStride + (lin % kPkWarps)];
+                s += cnt[q];
+            }
+            // CTA-wide exclusive scan of the per-thread sums
+            uint32_t inc = s;
+#pragma unroll
+            for (int dd = 1; dd < 32; dd <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, dd);
+                if (lane >= dd) inc += y;
+            }
+            if (lane == 31) ws[wp] = inc;
+            __syncthreads();
+            if (wp == 0) {
+                const uint32_t t = lane < kPkWarps ? ws[lane] : 0u;
+                uint32_t ti = t;
+#pragma unroll
+                for (int dd = 1; dd < 32; dd <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, ti, dd);
+                    if (lane >= dd) ti += y;
+                }
+                if (lane < kPkWarps) ws[lane] = ti - t;
+            }
+            __syncthreads();
+            uint32_t off = ws[wp] + inc - s;
+#pragma unroll
+            for (int q = 0; q < PER; ++q) {
+                const int lin = threadIdx.x * PER + q;
+                hist[(lin / kPkWarps) * kPkHistStride + (lin % kPkWarps)] = off;
+                off += cnt[q];
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const uint32_t dg = (c[j] >> sh) & (kPkRadix - 1);
+            const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+            const uint32_t base = hist[dg * kPkHistStride + wp];
+            __syncwarp();
+            if (lane == __ffs(peers) - 1) hist[dg * kPkHistStride + wp] = base + __popc(peers);
+            __syncwarp();
+            skey[base + __popc(peers & lt)] = c[j];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) c[j] = skey[pos0 + j * 32];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) skey[pos0 + j * 32] = c[j];
+    __syncthreads();
+
+    uint16_t *out = rows + (size_t)blockIdx.x * npad;
+    const int run = npad / 32;
+    if (L.dual) {
+        // bank-balanced copy choice per gather group (see k_sort_rows)
+        uint8_t *ld = reinterpret_cast<uint8_t *>(hist) + threadIdx.x;
+        for (int g = threadIdx.x; g < run; g += kPkThreads) {
+#pragma unroll
+            for (int b = 0; b < 32; ++b) ld[b * kPkThreads] = 0;
+            uint32_t mask = 0;
+            bool pad_seen = false;
+            for (int k = 0; k < 32; ++k) {
+                const int p = k * run + g;
+                if (p >= n) {
+                    if (!pad_seen) ld[(n & 31) * kPkThreads]++;
+                    pad_seen = true;
+                    continue;
+                }
+                const int i = (int)(skey[p] & imask);
+                const int ba = i & 31, bb = rot_b(i) & 31;
+                if (ld[bb * kPkThreads] < ld[ba * kPkThreads]) { ld[bb * kPkThreads]++; mask |= 1u << k; }
+                else ld[ba * kPkThreads]++;
+            }
+            for (int pass = 0; pass < 2; ++pass)
+                for (int k = 0; k < 32; ++k) {
+                    const int p = k * run + g;
+                    if (p >= n) break;
+                    const int i = (int)(skey[p] & imask);
+                    const int ba = i & 31, bb = rot_b(i) & 31;
+                    const bool onb = (mask >> k) & 1u;
+                    const int cur = onb ? bb : ba, oth = onb ? ba : bb;
+                    if (ld[cur * kPkThreads] > ld[oth * kPkThreads] + 1) {
+                        ld[cur * kPkThreads]--;
+                        ld[oth * kPkThreads]++;
+                        mask ^= 1u << k;
+                    }
+                }
+            gchoice[g] = mask;
+        }
+        __syncthreads();
+    }
+    for (int P = threadIdx.x; P < npad; P += kPkThreads) {
+        const int p = logical_of(P, run);
+        uint16_t e;
+        if (p < n) {
+            const uint32_t cp = skey[p];
+            const bool step = (p == n - 1) || ((cp >> ib) < (skey[p + 1] >> ib));
+            int word = (int)(cp & imask);
+            if (L.dual) {
+                const int k = (P >> 3) & 31, g = (P >> 8) * kChunkElems + (P & 7);
+                if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
+            }
+            e = static_cast<uint16_t>(word | (step ? kFlagBit : 0));
+        } else {
+            e = static_cast<uint16_t>(n);
+        }
+        out[P] = e;
+    }
+}
+
+template <int IPT>
+static size_t sort_packed_smem() {
+    return (size_t)kPkThreads * IPT * 4 + (size_t)(kPkHistWords + kMaxGroups + kPkWarps + 2) * 4;
+}
+
+template <int IPT>
+static cudaError_t launch_sort_packed(const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
+                                      int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows,
+                                      int npad, int32_t *flags, cudaStream_t st) {
+    const size_t sm = sort_packed_smem<IPT>();
+    cudaError_t e = cudaFuncSetAttribute(k_sort_rows_packed<IPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    k_sort_rows_packed<IPT><<<(unsigned)nf, kPkThreads, sm, st>>>(ii_t, ii_stride, w, feat, f0, L, rows, npad,
+                                                                   flags);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, const DevFeature *feat,
+                             int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows, int npad,
+                             int32_t *flags, cudaStream_t st) {
     if (nf <= 0) return cudaSuccess;
     const int n = L.n;
     // two weight copies need the bank-choice space, which the 32-item variant lacks
     if (L.dual && n > kSortThreads * 16) return cudaErrorInvalidValue;
-    if (n <= kSortThreads * 1) return launch_sort_ipt<1>(vals, L, nf, rows, npad, st);
-    if (n <= kSortThreads * 2) return launch_sort_ipt<2>(vals, L, nf, rows, npad, st);
-    if (n <= kSortThreads * 4) return launch_sort_ipt<4>(vals, L, nf, rows, npad, st);
-    if (n <= kSortThreads * 8) return launch_sort_ipt<8>(vals, L, nf, rows, npad, st);
-    if (n <= kSortThreads * 16) return launch_sort_ipt<16>(vals, L, nf, rows, npad, st);
-    return launch_sort_ipt<32>(vals, L, nf, rows, npad, st);
+    // packed items: 14-bit sample index, value span below 2^18
+    if (n <= kPkThreads * 32 && 255LL * w * h < (1LL << 18)) {
+#define VJB_PK_CASE(I) launch_sort_packed<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, flags, st)
+        const int ipt = (n + kPkThreads - 1) / kPkThreads;
+        if (ipt <= 4) return VJB_PK_CASE(4);
+        if (ipt <= 8) return VJB_PK_CASE(8);
+        if (ipt <= 12) return VJB_PK_CASE(12);
+        if (ipt <= 16) return VJB_PK_CASE(16);
+        if (ipt <= 20) return VJB_PK_CASE(20);
+        if (ipt <= 24) return VJB_PK_CASE(24);
+        if (ipt <= 28) return VJB_PK_CASE(28);
+        if (ipt <= 30) return VJB_PK_CASE(30);
+        return VJB_PK_CASE(32);
+#undef VJB_PK_CASE
+    }
+#define VJB_SORT_CASE(I) launch_sort_ipt<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, st)
+    if (n <= kSortThreads * 1) return VJB_SORT_CASE(1);
+    if (n <= kSortThreads * 2) return VJB_SORT_CASE(2);
+    if (n <= kSortThreads * 4) return VJB_SORT_CASE(4);
+    if (n <= kSortThreads * 8) return VJB_SORT_CASE(8);
+    if (n <= kSortThreads * 16) return VJB_SORT_CASE(16);
+    return VJB_SORT_CASE(32);
+#undef VJB_SORT_CASE
 }
 
 }  // namespace vjb

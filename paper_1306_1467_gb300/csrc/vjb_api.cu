@@ -445,23 +445,15 @@ int prepare_tables(vjb_ctx *c) {
         c->box_lines = 0;  // set with the search shape
     }
     if (!c->d_rows) CK(cudaMalloc(&c->d_rows, sizeof(uint16_t) * (size_t)c->nfeat * c->npad));
-    const int64_t tile = std::max<int64_t>(1, std::min<int64_t>(c->nfeat, (int64_t(1) << 28) / c->n));
-    int32_t *d_vals = nullptr;
-    CK(cudaMalloc(&d_vals, sizeof(int32_t) * (size_t)tile * c->n));
-    int err = VJB_OK;
-    for (int64_t f0 = 0; f0 < c->nfeat && err == VJB_OK; f0 += tile) {
+    // feature values (the K2 arithmetic, fused into the sort) and sort, a tile of rows per launch
+    const int64_t tile = std::max<int64_t>(1, std::min<int64_t>(c->nfeat, 65535));
+    for (int64_t f0 = 0; f0 < c->nfeat; f0 += tile) {
         const int64_t nf = std::min(tile, c->nfeat - f0);
-        cudaError_t e = launch_feature_values(c->d_ii, c->ii_stride, c->n, c->w, c->d_feat, f0, nf,
-                                              d_vals, c->stream);
-        if (e == cudaSuccess)
-            e = launch_sort_rows(d_vals, c->lay, nf, c->d_rows + (size_t)f0 * c->npad, c->npad, c->stream);
-        if (e != cudaSuccess) err = fail(VJB_ECUDA, "prepare launch failed: %s", cudaGetErrorString(e));
-        c->launches += 2;
+        CK(launch_sort_rows(c->d_ii, c->ii_stride, c->w, c->h, c->d_feat, f0, nf, c->lay,
+                            c->d_rows + (size_t)f0 * c->npad, c->npad, flags_ptr(c), c->stream));
+        c->launches += 1;
     }
-    cudaError_t se = cudaStreamSynchronize(c->stream);
-    cudaFree(d_vals);
-    if (err) return err;
-    if (se != cudaSuccess) return fail(VJB_ECUDA, "prepare failed: %s", cudaGetErrorString(se));
+    CK(cudaStreamSynchronize(c->stream));
     // the search kernels gather through the table without bounds checks: validate it once
     CK(launch_check_rows(c->d_rows, c->nfeat, c->lay, c->npad, flags_ptr(c), c->num_sms * 8, c->stream));
     c->launches += 1;

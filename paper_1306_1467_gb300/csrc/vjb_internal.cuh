@@ -130,8 +130,9 @@ cudaError_t launch_integral(const uint8_t *px, int n, int h, int w, int32_t *ii_
 cudaError_t launch_feature_values(const int32_t *ii_t, int ii_stride, int n, int w,
                                   const DevFeature *feat, int64_t f0, int64_t nf, int32_t *out,
                                   cudaStream_t st);
-cudaError_t launch_sort_rows(const int32_t *vals, const WeightLayout &L, int64_t nf, uint16_t *rows,
-                             int npad, cudaStream_t st);
+cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, const DevFeature *feat,
+                             int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows, int npad,
+                             int32_t *flags, cudaStream_t st);
 cudaError_t launch_check_rows(const uint16_t *rows, int64_t nfeat, const WeightLayout &L, int npad,
                               int32_t *flags, int grid, cudaStream_t st);
 cudaError_t launch_init_weights(const uint8_t *y, const WeightLayout &L, const float *w_in,
