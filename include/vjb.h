@@ -218,11 +218,11 @@ int vjb_screen_errors(vjb_ctx *ctx, float *out);
  * value.  Shapes whose shared memory does not fit one SM are rejected with
  * VJB_EINVAL.  Takes effect from the next round. */
 typedef struct {
-    int32_t warps;        /* consumer warps per CTA: 1-16 (1-8 with unroll 4)      */
-    int32_t stages;       /* TMA stages per warp: 2-8                              */
+    int32_t warps;        /* consumer warps per CTA: 1-20 (1-12 with unroll 4)     */
+    int32_t stages;       /* TMA stages per warp: 1-8                              */
     int32_t ctas_per_sm;  /* 1-4                                                   */
-    int32_t unroll;       /* 512-entry units a warp works on together: 1, 2 or 4   */
-    int32_t box_lines;    /* 128-byte lines per TMA box (stage): 8, 16 or 32       */
+    int32_t unroll;       /* 16-entry pieces a lane works on together: 1, 2 or 4   */
+    int32_t box_lines;    /* 128-byte lines per TMA box (stage): 4-32, a multiple of 4 */
 } vjb_search_shape;
 
 int vjb_set_search_shape(vjb_ctx *ctx, const vjb_search_shape *shape);

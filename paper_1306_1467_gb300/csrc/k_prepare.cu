@@ -335,32 +335,34 @@ __global__ void __launch_bounds__(kSortThreads, 1)
     }
 }
 
-// Validation of a finished table: every entry before position n names a
-// sample below n through a word of the weight array, every entry from n on is
-// the padding word n.  Sets kFlagBadTable in `flags` otherwise.  The search
+// Validation of a finished table: every entry before position n names a word
+// inside the weight array other than the padding word, every entry from n on
+// is the padding word n.  Sets kFlagBadTable in `flags` otherwise.  The search
 // kernels rely on this to gather weights without bounds checks.  One CTA per
 // row at a time, one 16-byte chunk (8 entries) per thread.
 __global__ void k_check_rows(const uint16_t *__restrict__ rows, int64_t nfeat, WeightLayout L,
                              int npad, int32_t *flags) {
     bool bad = false;
     const int n = L.n, run = npad / 32, nch = npad / kChunkElems;
+    const uint32_t words = (uint32_t)L.words, pad = (uint32_t)n;
     for (int64_t f = blockIdx.x; f < nfeat; f += gridDim.x) {
         const uint4 *row = reinterpret_cast<const uint4 *>(rows + (size_t)f * npad);
         for (int c = threadIdx.x; c < nch; c += blockDim.x) {
             const uint4 q = __ldg(row + c);
             const int p0 = (c & 31) * run + (c >> 5) * kChunkElems;  // logical position of entry 0
             const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
+            if (p0 + kChunkElems <= n) {
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
-                const int p = p0 + j;
-                const int word = (int)(e & kIndexMask);
-                if (p < n) {
-                    const bool ok = word < n || (L.dual && word >= L.off_b && word < L.words &&
-                                                 unrot_b(word - L.off_b) < n);
-                    bad |= !ok;
-                } else {
-                    bad |= e != (uint32_t)n;
+                for (int j = 0; j < 4; ++j) {
+                    const uint32_t a = wd[j] & kIndexMask, b = (wd[j] >> 16) & kIndexMask;
+                    bad |= a >= words || a == pad || b >= words || b == pad;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
+                    const uint32_t word = e & kIndexMask;
+                    bad |= (p0 + j < n) ? (word >= words || word == pad) : (e != pad);
                 }
             }
         }
@@ -537,24 +539,36 @@ __global__ void __launch_bounds__(kPkThreads, 2)
     uint16_t *out = rows + (size_t)blockIdx.x * npad;
     const int run = npad / 32;
     if (L.dual) {
-        // bank-balanced copy choice per gather group (see k_sort_rows)
-        uint8_t *ld = reinterpret_cast<uint8_t *>(hist) + threadIdx.x;
+        // bank-balanced copy choice per gather group (see k_sort_rows); the
+        // loads of the 32 banks live in registers as bit planes: bank b holds
+        // l1:b + l2:b + l3:b entries (a load above 3 counts as 3)
         for (int g = threadIdx.x; g < run; g += kPkThreads) {
-#pragma unroll
-            for (int b = 0; b < 32; ++b) ld[b * kPkThreads] = 0;
-            uint32_t mask = 0;
+            uint32_t l1 = 0, l2 = 0, l3 = 0, mask = 0;
+            auto level = [&](int b) { return ((l1 >> b) & 1u) + ((l2 >> b) & 1u) + ((l3 >> b) & 1u); };
+            auto inc = [&](int b) {
+                const uint32_t bit = 1u << b;
+                if (!(l1 & bit)) l1 |= bit;
+                else if (!(l2 & bit)) l2 |= bit;
+                else l3 |= bit;
+            };
+            auto dec = [&](int b) {
+                const uint32_t bit = 1u << b;
+                if (l3 & bit) l3 &= ~bit;
+                else if (l2 & bit) l2 &= ~bit;
+                else l1 &= ~bit;
+            };
             bool pad_seen = false;
             for (int k = 0; k < 32; ++k) {
                 const int p = k * run + g;
                 if (p >= n) {
-                    if (!pad_seen) ld[(n & 31) * kPkThreads]++;
+                    if (!pad_seen) inc(n & 31);  // the padding word, read as a broadcast
                     pad_seen = true;
                     continue;
                 }
                 const int i = (int)(skey[p] & imask);
                 const int ba = i & 31, bb = rot_b(i) & 31;
-                if (ld[bb * kPkThreads] < ld[ba * kPkThreads]) { ld[bb * kPkThreads]++; mask |= 1u << k; }
-                else ld[ba * kPkThreads]++;
+                if (level(bb) < level(ba)) { inc(bb); mask |= 1u << k; }
+                else inc(ba);
             }
             for (int pass = 0; pass < 2; ++pass)
                 for (int k = 0; k < 32; ++k) {
@@ -564,9 +578,9 @@ __global__ void __launch_bounds__(kPkThreads, 2)
                     const int ba = i & 31, bb = rot_b(i) & 31;
                     const bool onb = (mask >> k) & 1u;
                     const int cur = onb ? bb : ba, oth = onb ? ba : bb;
-                    if (ld[cur * kPkThreads] > ld[oth * kPkThreads] + 1) {
-                        ld[cur * kPkThreads]--;
-                        ld[oth * kPkThreads]++;
+                    if (level(cur) > level(oth) + 1) {
+                        dec(cur);
+                        inc(oth);
                         mask ^= 1u << k;
                     }
                 }

@@ -139,7 +139,7 @@ __device__ __forceinline__ void scan_pieces(uint32_t sbase, int t0, int lane, co
 }
 
 template <int U>
-__global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
+__global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     k_screen(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ v, int words,
              int lines_per_row, int box_lines, int stage_lines, int64_t nfeat,
              int stages, RoundState *rs, float *__restrict__ ferr, float *__restrict__ bmin) {
@@ -169,52 +169,51 @@ __global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
     const int64_t total = nf_w * nc;
     const uint32_t tx = (uint32_t)box_lines * kLineBytes;
 
-    auto issue = [&](int64_t seq) {
-        const int64_t k = seq / nc;
-        const int c = (int)(seq - k * nc);
-        const int64_t f = gw + k * G;
-        const int stage = (int)(seq % stages);
-        const uint32_t bar = bar_w + 8u * stage;
+    // producer state (lane 0): the next chunk to load, in this warp's order
+    int64_t pk = 0, issued = 0;
+    int pc = 0, pstage = 0;
+    auto issue_next = [&]() {
+        if (issued >= total) return;
+        const uint32_t bar = bar_w + 8u * (uint32_t)pstage;
         mbar_arrive_expect_tx(bar, tx);
-        tma_load_3d(ring_w + (uint32_t)stage * stage_bytes, &tmap, 0, c * box_lines, (int32_t)f, bar);
+        tma_load_3d(ring_w + (uint32_t)pstage * stage_bytes, &tmap, 0, pc * box_lines,
+                    (int32_t)(gw + pk * G), bar);
+        if (++pc == nc) { pc = 0; ++pk; }
+        if (++pstage == stages) pstage = 0;
+        ++issued;
     };
-    if (lane == 0) {
-        const int64_t pro = total < stages ? total : stages;
-        for (int64_t s = 0; s < pro; ++s) issue(s);
-    }
+    if (lane == 0)
+        for (int s = 0; s < stages; ++s) issue_next();
     __syncwarp();
 
     const float Tp = (float)rs->t_pos, Tm = (float)rs->t_neg;
     float best = INFINITY;
-    int64_t seq = 0;
+    int cstage = 0;
+    uint32_t cpar = 0;  // consumer ring position and mbarrier phase
+    int64_t consumed = 0;
     bool ok = true;
     for (int64_t k = 0; k < nf_w && ok; ++k) {
         const int64_t f = gw + k * G;
         float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
         for (int c = 0; c < nc; ++c) {
-            const int stage = (int)(seq % stages);
-            const uint32_t par = (uint32_t)((seq / stages) & 1);
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * stage, par))) {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
                 ok = false;
                 break;
             }
             const int lines_here = min(box_lines, lines_per_row - c * box_lines);
             const int crs = lines_here >> 2;  // chunk rows (a line is a quarter of one)
-            const uint32_t sbase = ring_w + (uint32_t)stage * stage_bytes;
-            if (crs == 8) {
-#pragma unroll
-                for (int t = 0; t < 8; t += 2 * U) scan_pieces<U, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
-            } else {
-                int t = 0;
-                for (; t + 2 <= crs; t += 2) scan_pieces<1, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
-                if (t < crs) scan_pieces<1, 1>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
-            }
+            const uint32_t sbase = ring_w + (uint32_t)cstage * stage_bytes;
+            int t = 0;
+            for (; t + 2 * U <= crs; t += 2 * U) scan_pieces<U, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+            for (; t + 2 <= crs; t += 2) scan_pieces<1, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+            if (t < crs) scan_pieces<1, 1>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
             __syncwarp();
-            if (lane == 0 && seq + stages < total) {
+            if (lane == 0) {
                 fence_proxy_async_smem();
-                issue(seq + stages);
+                issue_next();
             }
-            ++seq;
+            if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
+            ++consumed;
         }
         if (!ok) break;
         // the runs of the lanes below come first: exclusive scan of the run totals
@@ -240,10 +239,14 @@ __global__ void __launch_bounds__(U >= 4 ? 256 : 512, 1)
         // stop: record the failure and wait (bounded) for this warp's copies in flight
         if (lane == 0) {
             atomicOr(&rs->flags, kFlagWaitTimeout);
-            const int64_t issued = (seq + stages < total) ? seq + stages : total;
-            for (int64_t s = seq; s < issued; ++s)
-                mbar_wait_bounded(bar_w + 8u * (uint32_t)(s % stages), (uint32_t)((s / stages) & 1),
-                                  100000000ull);
+            // chunks issued but not consumed sit in the ring from the current stage on
+            int st = cstage;
+            uint32_t ph = cpar;
+            const int64_t pending = issued - consumed;
+            for (int64_t s = 0; s < pending; ++s) {
+                mbar_wait_bounded(bar_w + 8u * (uint32_t)st, ph, 100000000ull);
+                if (++st == stages) { st = 0; ph ^= 1u; }
+            }
         }
         __syncwarp();
     }
@@ -284,7 +287,7 @@ cudaError_t set_screen_smem_limit(int bytes) {
     return e;
 }
 
-int screen_max_warps(int unroll) { return unroll >= 4 ? 8 : 16; }
+int screen_max_warps(int unroll) { return unroll >= 4 ? 12 : 20; }
 
 int screen_occupancy(const SearchShape &s, int words) {
     int blocks = 0;

@@ -92,7 +92,7 @@ struct vjb_ctx {
     std::vector<vjb_feature> feats;
     CUtensorMap tmap;
     bool tmap_ok = false;
-    SearchShape shape{12, 2, 1, 2, 32};
+    SearchShape shape{12, 2, 1, 4, 32};
     bool shape_set = false;
     int screen_grid = 0, shortlist_grid = 0, rescan_grid = 0;
 
@@ -210,10 +210,11 @@ int apply_shape(vjb_ctx *c) {
 
 int choose_default_shape(vjb_ctx *c) {
     if (c->shape_set && shape_fits(c, c->shape)) return apply_shape(c);
-    // measured on the 24x24 / 15k workload: more warps with two stages beat deeper rings
-    const SearchShape tries[] = {{12, 2, 1, 2, 32}, {16, 2, 1, 2, 16}, {8, 3, 1, 2, 32}, {8, 2, 1, 2, 32},
-                                 {6, 3, 1, 2, 32}, {4, 4, 1, 2, 32}, {4, 2, 1, 2, 32}, {2, 2, 1, 2, 16},
-                                 {2, 2, 1, 1, 8}};
+    // measured on the 24x24 / 15k workload: as many warps as shared memory allows,
+    // two stages of 4 KiB, four pieces in flight per lane
+    const SearchShape tries[] = {{12, 2, 1, 4, 32}, {12, 2, 1, 2, 32}, {16, 2, 1, 2, 24}, {8, 3, 1, 4, 32},
+                                 {8, 2, 1, 4, 32}, {6, 3, 1, 2, 32}, {4, 4, 1, 2, 32}, {4, 2, 1, 2, 32},
+                                 {2, 2, 1, 2, 16}, {2, 2, 1, 1, 8}};
     for (const auto &s : tries)
         if (shape_fits(c, s)) {
             c->shape = s;
@@ -815,9 +816,9 @@ int vjb_set_search_shape(vjb_ctx *c, const vjb_search_shape *in) {
     if (in->ctas_per_sm) s.ctas_per_sm = in->ctas_per_sm;
     if (in->unroll) s.unroll = in->unroll;
     if (in->box_lines) s.box_lines = in->box_lines;
-    if (s.warps < 1 || s.warps > 16 || s.stages < 2 || s.stages > 8 || s.ctas_per_sm < 1 || s.ctas_per_sm > 4 ||
+    if (s.warps < 1 || s.warps > 20 || s.stages < 1 || s.stages > 8 || s.ctas_per_sm < 1 || s.ctas_per_sm > 4 ||
         (s.unroll != 1 && s.unroll != 2 && s.unroll != 4) || s.warps > screen_max_warps(s.unroll) ||
-        (s.box_lines != 8 && s.box_lines != 16 && s.box_lines != 32) || 8 * s.unroll > s.box_lines)
+        s.box_lines < 4 || s.box_lines > 32 || s.box_lines % 4 != 0)
         return fail(VJB_EINVAL, "search shape (%d warps, %d stages, %d CTAs/SM, unroll %d, box %d lines) out of range",
                     s.warps, s.stages, s.ctas_per_sm, s.unroll, s.box_lines);
     if (c->n > 0 && !shape_fits(c, s))
