@@ -74,6 +74,24 @@ typedef struct {
     double  alpha;      /* +inf when error == 0                           */
 } vjb_stump;
 
+/* What the search saw of one kept round's stump (precision diagnostics),
+ * each divided by the round's FP64 weight total so that it compares with the
+ * stump record's `error` (the FP64 sum).
+ * search_error: the stump's weighted error from the compensated (double-float
+ *   FP32) re-scan that chose it.
+ * screen_error: the FP32 screened error of the stump's feature.
+ * screen_min:   the smallest FP32 screened error of the round.
+ * candidates:   features re-scanned compensated in the round.
+ * forced:       1 if the round's stump came from vjb_force_stump (the other
+ *   fields then repeat the FP64 error and candidates is 0). */
+typedef struct {
+    double  search_error;
+    float   screen_error;
+    float   screen_min;
+    int32_t candidates;
+    int32_t forced;
+} vjb_round_diag;
+
 /* Diagnostics of the context and of its last search. */
 typedef struct {
     int32_t n, h, w;          /* samples and window size                        */
@@ -227,6 +245,10 @@ typedef struct {
 
 int vjb_set_search_shape(vjb_ctx *ctx, const vjb_search_shape *shape);
 int vjb_get_search_shape(vjb_ctx *ctx, vjb_search_shape *out);
+
+/* Round diagnostics of kept rounds [first, first + count) into out (host).
+ * Errors: VJB_EINVAL for a range outside the kept rounds; VJB_ESTATE. */
+int vjb_get_round_diag(vjb_ctx *ctx, int32_t first, int32_t count, vjb_round_diag *out);
 
 /* ---- timing ------------------------------------------------------------------
  * vjb_set_timing: enable (1) or disable (0) event timing of rounds; enabling

@@ -519,6 +519,8 @@ __global__ void __launch_bounds__(kRescanWarps * 32)
             rs->win_feature = b.feature;
             rs->win_split = b.split;
             rs->win_polarity = b.polarity;
+            rs->win_err_hi = b.err_hi;
+            rs->win_err_lo = b.err_lo;
         }
         rs->done_rescan = 0u;
     }

@@ -129,7 +129,8 @@ __global__ void __launch_bounds__(kUpdateThreads)
     k_update_a(const uint16_t *__restrict__ rows, int npad, WeightLayout L,
                const int32_t *__restrict__ ii_t, int ii_stride, int w, const DevFeature *__restrict__ feat,
                const uint8_t *__restrict__ y, const float *__restrict__ wts, uint8_t *__restrict__ miss,
-               double *partials, RoundState *rs, vjb_stump *stumps, int stump_cap, vjb_stump *last) {
+               double *partials, RoundState *rs, vjb_stump *stumps, vjb_round_diag *diag,
+               int stump_cap, vjb_stump *last, const float *__restrict__ ferr) {
     if (rs->status != VJB_OK) return;
     const int n = L.n;
     const bool forced = rs->forced != 0;
@@ -191,6 +192,15 @@ __global__ void __launch_bounds__(kUpdateThreads)
     st.polarity = p;
     st.split = split;
     st.error = eps;
+    // what the search saw of this stump, next to its FP64 error; the search
+    // works in units of the current weight total T, so divide by it
+    vjb_round_diag dg;
+    dg.search_error = forced ? eps : ((double)rs->win_err_hi + (double)rs->win_err_lo) / T;
+    dg.screen_error = forced ? (float)eps : (float)((double)ferr[f] / T);
+    dg.screen_min = forced ? (float)eps : (float)((double)rs->screen_min / T);
+    dg.candidates = forced ? 0 : rs->cand_count;
+    dg.forced = forced ? 1 : 0;
+    if (rs->rounds < stump_cap) diag[rs->rounds] = dg;
     rs->last_cands = rs->cand_count;
     rs->cand_count = 0;
     rs->forced = 0;
@@ -254,11 +264,11 @@ __global__ void __launch_bounds__(kUpdateThreads)
 cudaError_t launch_update_a(const uint16_t *rows, int npad, const WeightLayout &L,
                             const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
                             const uint8_t *y, const float *wts, uint8_t *miss, double *partials,
-                            RoundState *rs, vjb_stump *stumps, int stump_cap, vjb_stump *last,
-                            cudaStream_t st) {
+                            RoundState *rs, vjb_stump *stumps, vjb_round_diag *diag, int stump_cap,
+                            vjb_stump *last, const float *ferr, cudaStream_t st) {
     k_update_a<<<update_grid(L.n), kUpdateThreads, 0, st>>>(rows, npad, L, ii_t, ii_stride, w, feat, y,
-                                                            wts, miss, partials, rs, stumps, stump_cap,
-                                                            last);
+                                                            wts, miss, partials, rs, stumps, diag,
+                                                            stump_cap, last, ferr);
     return cudaGetLastError();
 }
 

@@ -86,6 +86,7 @@ struct vjb_ctx {
     double *d_partials = nullptr;
     RoundState *d_rs = nullptr;
     vjb_stump *d_stumps = nullptr, *d_last = nullptr;
+    vjb_round_diag *d_diag = nullptr;
     int stump_cap = 0;
     int bmin_cap = 0;
 
@@ -117,7 +118,7 @@ struct vjb_ctx {
         dfree(d_px); dfree(d_y); dfree(d_ii); dfree(d_feat); dfree(d_rows);
         dfree(d_w); dfree(d_v); dfree(d_wtmp); dfree(d_ferr); dfree(d_bmin); dfree(d_cand);
         dfree(d_cand_ids); dfree(d_miss); dfree(d_partials);
-        dfree(d_rs); dfree(d_stumps); dfree(d_last);
+        dfree(d_rs); dfree(d_stumps); dfree(d_last); dfree(d_diag);
         stump_cap = bmin_cap = 0;
         feats.clear();
         stage = kStageNone;
@@ -228,12 +229,18 @@ int ensure_stump_cap(vjb_ctx *c, int need) {
     int cap = std::max(1024, c->stump_cap);
     while (cap < need) cap *= 2;
     vjb_stump *p = nullptr;
+    vjb_round_diag *q = nullptr;
     CK(cudaMalloc(&p, sizeof(vjb_stump) * cap));
-    if (c->d_stumps && c->stump_cap)
+    CK(cudaMalloc(&q, sizeof(vjb_round_diag) * cap));
+    if (c->d_stumps && c->stump_cap) {
         CK(cudaMemcpyAsync(p, c->d_stumps, sizeof(vjb_stump) * c->stump_cap, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(q, c->d_diag, sizeof(vjb_round_diag) * c->stump_cap, cudaMemcpyDeviceToDevice, c->stream));
+    }
     CK(cudaStreamSynchronize(c->stream));
     dfree(c->d_stumps);
+    dfree(c->d_diag);
     c->d_stumps = p;
+    c->d_diag = q;
     c->stump_cap = cap;
     c->drop_graph();
     return VJB_OK;
@@ -275,8 +282,8 @@ int collect_timing(vjb_ctx *c) {
 // round).  `ev` (may be NULL) brackets the search kernel and the round.
 int enqueue_update(vjb_ctx *c) {
     CK(launch_update_a(c->d_rows, c->npad, c->lay, c->d_ii, c->ii_stride, c->w, c->d_feat, c->d_y,
-                       c->d_w, c->d_miss, c->d_partials, c->d_rs, c->d_stumps, c->stump_cap,
-                       c->d_last, c->stream));
+                       c->d_w, c->d_miss, c->d_partials, c->d_rs, c->d_stumps, c->d_diag, c->stump_cap,
+                       c->d_last, c->d_ferr, c->stream));
     CK(launch_update_b(c->lay, c->d_y, c->d_w, c->d_v, c->d_miss, c->d_partials, c->d_rs, c->stream));
     return VJB_OK;
 }
@@ -842,6 +849,23 @@ int vjb_get_search_shape(vjb_ctx *c, vjb_search_shape *out) {
     out->ctas_per_sm = c->shape.ctas_per_sm;
     out->unroll = c->shape.unroll;
     out->box_lines = c->shape.box_lines;
+    return VJB_OK;
+}
+
+int vjb_get_round_diag(vjb_ctx *c, int32_t first, int32_t count, vjb_round_diag *out) {
+    g_err[0] = 0;
+    if (!c || !out) return fail(VJB_EINVAL, "NULL argument");
+    if (c->stage < kStageLoaded) return fail(VJB_ESTATE, "no training set loaded");
+    int rc = set_dev(c);
+    if (rc) return rc;
+    RoundState rs;
+    rc = read_state(c, &rs);
+    if (rc) return rc;
+    if (first < 0 || count < 0 || first + count > rs.rounds || first + count > c->stump_cap)
+        return fail(VJB_EINVAL, "rounds [%d, %d) outside the %d kept", first, first + count, rs.rounds);
+    if (count == 0) return VJB_OK;
+    CK(cudaMemcpyAsync(out, c->d_diag + first, sizeof(vjb_round_diag) * count, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
     return VJB_OK;
 }
 

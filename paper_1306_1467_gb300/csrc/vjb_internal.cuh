@@ -58,6 +58,7 @@ struct RoundState {
     int32_t forced_feature, forced_threshold, forced_polarity;
     int32_t win_feature, win_split, win_polarity;  // the round's stump
     uint32_t done_rescan, done_update_a, done_update_b;  // last-CTA counters
+    float win_err_hi, win_err_lo;  // the stump's error from the compensated re-scan
     int32_t pad;
 };
 
@@ -148,8 +149,8 @@ cudaError_t launch_rescan(const uint16_t *rows, int npad, const float *v, const 
 cudaError_t launch_update_a(const uint16_t *rows, int npad, const WeightLayout &L,
                             const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
                             const uint8_t *y, const float *wts, uint8_t *miss, double *partials,
-                            RoundState *rs, vjb_stump *stumps, int stump_cap, vjb_stump *last,
-                            cudaStream_t st);
+                            RoundState *rs, vjb_stump *stumps, vjb_round_diag *diag, int stump_cap,
+                            vjb_stump *last, const float *ferr, cudaStream_t st);
 cudaError_t launch_update_b(const WeightLayout &L, const uint8_t *y, float *wts, float *v,
                             const uint8_t *miss, double *partials, RoundState *rs,
                             cudaStream_t st);

@@ -61,6 +61,14 @@ class Info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
 
 
+class RoundDiag(C.Structure):
+    _fields_ = [("search_error", C.c_double), ("screen_error", C.c_float), ("screen_min", C.c_float),
+                ("candidates", C.c_int32), ("forced", C.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class SearchShapeC(C.Structure):
     _fields_ = [("warps", C.c_int32), ("stages", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("unroll", C.c_int32), ("box_lines", C.c_int32)]
@@ -97,6 +105,7 @@ SIGNATURES = {
     "vjb_screen_errors": (C.c_int, [_P, _P]),
     "vjb_set_search_shape": (C.c_int, [_P, _P]),
     "vjb_get_search_shape": (C.c_int, [_P, _P]),
+    "vjb_get_round_diag": (C.c_int, [_P, _I32, _I32, _P]),
     "vjb_set_timing": (C.c_int, [_P, _I32]),
     "vjb_get_timing": (C.c_int, [_P, _P]),
     "vjb_screen_noalloc": (C.c_int, [_P, _P, _I32, _I32, _I64, C.c_double, C.c_double, _I32,
@@ -264,6 +273,14 @@ class Trainer:
         sh = SearchShapeC()
         self._check(self._lib.vjb_get_search_shape(self._h, C.byref(sh)))
         return {k: getattr(sh, k) for k, _ in sh._fields_}
+
+    def round_diag(self, first: int = 0, count: int | None = None) -> list:
+        """Per-round search diagnostics of kept rounds [first, first + count)."""
+        if count is None:
+            count = self.info()["rounds_done"] - first
+        arr = (RoundDiag * max(int(count), 1))()
+        self._check(self._lib.vjb_get_round_diag(self._h, int(first), int(count), arr))
+        return [arr[k].as_dict() for k in range(int(count))]
 
     def set_timing(self, enable: bool = True):
         """Enable (and reset) CUDA-event timing of every round's search kernel."""

@@ -320,3 +320,34 @@ def test_paper_shape_full_round_parity(paper_gpu):
         assert (s["feature"], s["threshold"], s["polarity"]) == (ref["feature"], ref["threshold"], ref["polarity"])
     ferr = tr.screen_errors().astype(np.float64)
     assert np.max(np.abs(ferr - best["err"])) <= SCREEN_TOL
+
+
+def test_precision_form_mid_size():
+    """Precision form at 16x16 / 3000 windows (32,384 features): weights
+    log-uniform in [1e-12, 1].  Each round on the same FP32 weights: the FP64
+    error matches the oracle within 1e-6, the stump matches unless near-tied,
+    the compensated-FP32 search error matches the FP64 error to double-float
+    accuracy and the FP32 screened error within the screening bound."""
+    from paper_1306_1467_gb300 import vjb
+    px, y = synth.make_windows(1000, 2000, 16, 16, seed=1310)
+    P = O.Prepared(px, y)
+    with _trainer() as tr:
+        tr.prepare(px, y)
+        tr.set_weights(synth.log_uniform_weights(y.shape[0], seed=1311))
+        stumps = []
+        for t in range(12):
+            wn = O.normalize(tr.get_weights().astype(np.float64))
+            ref = O.select(O.feature_best_sorted(P.vals, P.order, y, wn))
+            st, s = tr.train_round()
+            assert st == vjb.OK
+            assert abs(s["error"] - ref["err"]) <= REL * ref["err"], (t, s, ref)
+            if ref["second_err"] - ref["err"] > REL * ref["err"]:
+                assert (s["feature"], s["threshold"], s["polarity"]) == (ref["feature"], ref["threshold"], ref["polarity"])
+            stumps.append(s)
+        diag = tr.round_diag()
+        assert len(diag) == 12
+        for s, d in zip(stumps, diag):
+            assert d["forced"] == 0 and d["candidates"] >= 1
+            assert abs(d["search_error"] - s["error"]) <= 1e-9 * s["error"]
+            assert abs(d["screen_error"] - s["error"]) <= SCREEN_TOL
+            assert d["screen_min"] <= d["screen_error"]
