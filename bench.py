@@ -50,6 +50,12 @@ def _args():
                    help="precision form: 300 rounds from log-uniform weights, search vs FP64")
     p.add_argument("--oracle-rounds", type=int, default=6,
                    help="precision form: rounds checked against the full FP64 oracle")
+    p.add_argument("--batch", action="store_true",
+                   help="batching form only: 64 uneven 24x24 jobs batched against the plain path")
+    p.add_argument("--batch-jobs", type=int, default=64)
+    p.add_argument("--batch-rounds", type=int, default=100)
+    p.add_argument("--batch-n", type=int, nargs=2, default=(2000, 20000), metavar=("LO", "HI"),
+                   help="batching form: range of the jobs' sample counts")
     return p.parse_args()
 
 
@@ -417,11 +423,94 @@ def run_precision_report(a):
     print(json.dumps(line), flush=True)
 
 
+def batch_comparison(a, device: int = 0) -> dict:
+    """Batching form: `--batch-jobs` independent 24x24 jobs (N uniform in
+    2,000..20,000, positive fraction 0.2..0.5), `--batch-rounds` rounds each,
+    trained (1) one after another through the plain path and (2) together in
+    one batch (one launch of each round kernel per round, CUDA graph, launch
+    shape from the batch autotuner).  Reports both throughputs on this GPU and
+    whether every job's stumps are identical in the two."""
+    import torch
+
+    from paper_1306_1467_gb300 import synth, vjb
+
+    shapes = synth.batch_jobs(a.batch_jobs, seed=1309, n_lo=a.batch_n[0], n_hi=a.batch_n[1])
+    data = [synth.make_windows(p, q, h, w, seed=sd) for (p, q, h, w, sd) in shapes]
+    R = a.batch_rounds
+    nf = None
+    byts = []
+    # (1) plain: one context, the jobs one after another; rounds timed on the device
+    stream = torch.cuda.Stream(device=device)
+    plain_ms, plain_stumps = 0.0, []
+    with vjb.Trainer(device, stream=stream.cuda_stream) as tr:
+        for px, y in data:
+            nf = tr.prepare(px, y).shape[0]
+            byts.append(2.0 * nf * px.shape[0])
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, stumps = tr.train_strong(R)
+            e1.record(stream)
+            e1.synchronize()
+            plain_ms += e0.elapsed_time(e1)
+            plain_stumps.append(stumps)
+    torch.cuda.synchronize(device)
+    # (2) batched
+    budget = sum(vjb.Batch.table_bytes(px.shape[0], px.shape[1], px.shape[2]) for px, _ in data)
+    t0 = time.perf_counter()
+    b = vjb.Batch(budget, device=device)
+    ids = [b.add_job(px, y, R) for px, y in data]
+    setup_s = time.perf_counter() - t0
+    tuned = b.autotune(trial_rounds=2)
+    b_trials = b.trials
+    info = b.info()
+    b.set_timing(True)
+    t1 = time.perf_counter()
+    rest = b.train()
+    batch_s = time.perf_counter() - t1
+    tm = b.timing()
+    equal = sum(b.stumps(j) == ps for j, ps in zip(ids, plain_stumps))
+    b.close()
+    peak, peak_src = _peak()
+    round_bytes = sum(byts)
+    plain_rps = len(data) * R / (plain_ms / 1000.0)
+    batch_rps = len(data) * rest / batch_s if rest else 0.0
+    gbs = round_bytes * rest / batch_s / 1e9
+    search_ms = tm["search_ms_total"] / max(tm["rounds"], 1)
+    search_gbs = round_bytes / (search_ms / 1000.0) / 1e9 if tm["rounds"] else 0.0
+    return {"workload": f"{len(data)} jobs, 24x24, N uniform {a.batch_n[0]}-{a.batch_n[1]} "
+                        f"(sum {sum(p + q for p, q, *_ in shapes)}), "
+                        f"positive fraction 0.2-0.5, {R} rounds each, seed 1309",
+            "features_per_job": nf, "table_bytes": budget,
+            "plain": {"job_rounds_per_s": plain_rps, "ms_rounds_total": plain_ms,
+                      "gbs": round_bytes * R / (plain_ms / 1000.0) / 1e9},
+            "batched": {"job_rounds_per_s": batch_rps, "batch_round_ms": 1000.0 * batch_s / max(rest, 1),
+                        "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_source": f"{peak_src} hbm_gbs",
+                        "rounds_timed": rest, "autotune_rounds": tuned,
+                        "shape": {**{k: info[k] for k in ("warps", "stages", "unroll")},
+                                  "schedule": ("interleaved" if info["rows_per_warp"] < 0 else
+                                               f"work queue, {info['rows_per_warp']} rows per warp and item")},
+                        "setup_s": setup_s, "launches_per_round": 6,
+                        "roofline": {"kernel": "k_bscreen", "bound": "hbm", "achieved": search_gbs, "peak": peak,
+                                     "unit": "GB/s", "frac": search_gbs / peak,
+                                     "algorithmic_bytes_per_launch": round_bytes, "avg_launch_ms": search_ms,
+                                     "min_launch_ms": tm["search_ms_min"], "max_launch_ms": tm["search_ms_max"],
+                                     "launches_timed": tm["rounds"],
+                                     "round_ms": tm["round_ms_total"] / max(tm["rounds"], 1)}},
+            "autotune_trials": b_trials,
+            "speedup": batch_rps / plain_rps,
+            "identical_jobs": f"{equal}/{len(data)}"}
+
+
 def main():
     a = _args()
     ws, rank, local = _dist()
     if a.precision:
         run_precision_report(a)
+        return
+    if a.batch:
+        print(json.dumps({"metric": "batching form: batched vs plain on one GPU", **batch_comparison(a, local)}),
+              flush=True)
         return
     if a.impl == "reference":
         run_reference(a, ws, rank)

@@ -39,6 +39,7 @@ extern "C" {
 #define VJB_ENOMEM      (-3)  /* device allocation failed                             */
 #define VJB_ECUDA       (-4)  /* CUDA runtime / driver error                          */
 #define VJB_EDEVICE     (-5)  /* a kernel set its error flag (wait timeout, bounds)   */
+#define VJB_EFULL       (-6)  /* a batch has no room left (table budget, job slots)   */
 
 /* Limits.  Sample indices are stored in 15 bits and index N marks padding. */
 #define VJB_MAX_SAMPLES 32766
@@ -256,6 +257,94 @@ int vjb_get_round_diag(vjb_ctx *ctx, int32_t first, int32_t count, vjb_round_dia
  * rounds run since (host `out`).  Errors: VJB_EINVAL; VJB_ECUDA. */
 int vjb_set_timing(vjb_ctx *ctx, int32_t enable);
 int vjb_get_timing(vjb_ctx *ctx, vjb_timing *out);
+
+/* ---- batches: many jobs per launch ------------------------------------------------
+ * A batch trains many independent jobs (each its own windows, labels and
+ * number of rounds) with one launch of each round kernel for all of them,
+ * replayed as one CUDA graph per round.  Each job computes exactly what it
+ * computes alone in a context (same kernels per row and per block): its
+ * stumps and weights are bit-identical to a plain run.
+ * The batch owns an HBM arena of `table_budget_bytes` for the jobs' sorted
+ * tables (2 * F * npad bytes each, see vjb_batch_table_bytes); a job whose
+ * table does not fit the free arena is rejected with VJB_EFULL.  Everything
+ * else of a job lives in its own context, allocated when it is added.
+ * At most 256 jobs; a job's n must leave its weights within 32768 floats
+ * (every n up to VJB_MAX_SAMPLES does). */
+typedef struct vjb_batch vjb_batch;
+
+typedef struct {
+    int32_t jobs;               /* jobs in the batch                                  */
+    int32_t warps, stages, unroll, rows_per_warp;  /* search launch shape and schedule */
+    int32_t pad;
+    int64_t budget_bytes;       /* the table arena                                    */
+    int64_t free_bytes;         /* free arena                                         */
+    int64_t largest_free_bytes; /* largest free block (the largest table that fits)   */
+    double  search_bytes;       /* algorithmic bytes of one batched search: sum 2 F N */
+    int64_t launches;           /* kernels the batch has launched                     */
+} vjb_batch_info;
+
+/* Create a batch on `device` (stream may be NULL) with a table arena of
+ * `table_budget_bytes`.  Errors: VJB_EINVAL, VJB_ENOMEM, VJB_ECUDA. */
+int vjb_batch_create(vjb_batch **out, int device, void *cuda_stream, int64_t table_budget_bytes);
+void vjb_batch_destroy(vjb_batch *b);
+
+/* Arena bytes the sorted table of an n-sample h x w job needs. */
+int vjb_batch_table_bytes(int32_t n, int32_t h, int32_t w, int64_t *bytes);
+
+/* Add a job: copies its windows and labels (host, as vjb_load_windows),
+ * builds its integral images, features and sorted table (in the arena) and
+ * sets the Table 2 weights.  It will be trained until it has kept `rounds`
+ * stumps (or training ends).  *job_id receives its id.  Errors: VJB_EFULL
+ * (arena or slots), the errors of vjb_load_windows / vjb_enumerate_haar. */
+int vjb_batch_add_job(vjb_batch *b, const uint8_t *pixels, const uint8_t *labels, int32_t n,
+                      int32_t h, int32_t w, int32_t rounds, int32_t *job_id);
+
+/* Remove a job and free its table space.  Errors: VJB_EINVAL (unknown id). */
+int vjb_batch_remove_job(vjb_batch *b, int32_t job_id);
+
+/* Run up to `max_rounds` batched rounds: every job that has kept fewer
+ * stumps than its `rounds` and is not done takes part in each.
+ * *rounds_run (may be NULL) receives the rounds launched.  Errors:
+ * VJB_EDEVICE, VJB_ECUDA. */
+int vjb_batch_train(vjb_batch *b, int32_t max_rounds, int32_t *rounds_run);
+
+/* Autotuner of the batched search: times `trial_rounds` real rounds (after
+ * one untimed round) with each of a list of launch shapes (warps, stages,
+ * unroll, features per warp and work item) and keeps the fastest.  The rounds
+ * count toward the jobs' training, whose results do not depend on the shape;
+ * it stops trying when the jobs have fewer rounds left than a trial needs.
+ * *rounds_run (may be NULL) receives the rounds it ran; `trials` (may be
+ * NULL) up to `max_trials` timed shapes and *n_trials (may be NULL) their
+ * number. */
+typedef struct {
+    int32_t warps, stages, unroll, rows_per_warp;  /* the shape tried                  */
+    float   ms_per_round;                          /* its timed rounds, on the device  */
+} vjb_batch_trial;
+int vjb_batch_autotune(vjb_batch *b, int32_t trial_rounds, int32_t *rounds_run, vjb_batch_trial *trials,
+                       int32_t max_trials, int32_t *n_trials);
+
+/* A job's kept stumps so far and its status (VJB_OK, VJB_DONE_*, or a
+ * negative code if a kernel flagged it). */
+int vjb_batch_job_state(vjb_batch *b, int32_t job_id, int32_t *rounds_done, int32_t *status);
+
+/* A job's kept stumps [first, first + count) and its current weights (host). */
+int vjb_batch_get_stumps(vjb_batch *b, int32_t job_id, int32_t first, int32_t count, vjb_stump *out);
+int vjb_batch_get_weights(vjb_batch *b, int32_t job_id, float *out);
+
+/* Launch shape of the batched search (box height is always 32 lines) and its
+ * schedule: rows_per_warp > 0 hands out work items of that many features per
+ * warp from a queue; VJB_BATCH_INTERLEAVED (the default) gives warp w of the
+ * grid rows w, w + G, ... of every job in turn (G warps in the grid), the
+ * plain search's order, with no barrier between a CTA's rows of one job.
+ * A field or rows_per_warp of 0 keeps its value. */
+#define VJB_BATCH_INTERLEAVED (-1)
+int vjb_batch_set_search_shape(vjb_batch *b, const vjb_search_shape *shape, int32_t rows_per_warp);
+int vjb_batch_get_info(vjb_batch *b, vjb_batch_info *out);
+
+/* CUDA-event timing of every batched round: as vjb_set_timing / vjb_get_timing
+ * (enabling resets the totals; search = the batched search kernel). */
+int vjb_batch_set_timing(vjb_batch *b, int32_t enable);
+int vjb_batch_get_timing(vjb_batch *b, vjb_timing *out);
 
 /* ---- allocation-free search ----------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers

@@ -138,6 +138,38 @@ __device__ __forceinline__ void scan_pieces(uint32_t sbase, int t0, int lane, co
     }
 }
 
+// ---- shared pieces of the search kernels -----------------------------------------------
+
+// All chunk rows of one stage.
+template <int U>
+__device__ __forceinline__ void scan_stage(uint32_t sbase, int crs, int lane, const float *sv,
+                                           float &ahi, float &alo, float &bmx, float &bmn) {
+    int t = 0;
+    for (; t + 2 * U <= crs; t += 2 * U) scan_pieces<U, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+    for (; t + 2 <= crs; t += 2) scan_pieces<1, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+    if (t < crs) scan_pieces<1, 1>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+}
+
+// End of a row: the runs of the lanes below come first, so an exclusive
+// double-float scan of the run totals offsets each lane's best prefixes; the
+// feature's error is min(T+ - max D, T- + min D), split 0 (D = 0) included.
+__device__ __forceinline__ float finish_row(float ahi, float alo, float bmx, float bmn, float Tp,
+                                            float Tm, int lane) {
+    DF x{ahi, alo};
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const DF y = df_shfl_up(x, d);
+        if (lane >= d) x = df_add(y, x);
+    }
+    DF excl = df_shfl_up(x, 1);
+    if (lane == 0) excl = DF{0.f, 0.f};
+    float MX = warp_max(excl.hi + (excl.lo + bmx));
+    float MN = warp_min(excl.hi + (excl.lo + bmn));
+    MX = fmaxf(MX, 0.f);
+    MN = fminf(MN, 0.f);
+    return fminf(Tp - MX, Tm + MN);
+}
+
 template <int U>
 __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     k_screen(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ v, int words,
@@ -203,10 +235,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
             const int lines_here = min(box_lines, lines_per_row - c * box_lines);
             const int crs = lines_here >> 2;  // chunk rows (a line is a quarter of one)
             const uint32_t sbase = ring_w + (uint32_t)cstage * stage_bytes;
-            int t = 0;
-            for (; t + 2 * U <= crs; t += 2 * U) scan_pieces<U, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
-            for (; t + 2 <= crs; t += 2) scan_pieces<1, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
-            if (t < crs) scan_pieces<1, 1>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+            scan_stage<U>(sbase, crs, lane, sv, ahi, alo, bmx, bmn);
             __syncwarp();
             if (lane == 0) {
                 fence_proxy_async_smem();
@@ -216,20 +245,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
             ++consumed;
         }
         if (!ok) break;
-        // the runs of the lanes below come first: exclusive scan of the run totals
-        DF x{ahi, alo};
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const DF y = df_shfl_up(x, d);
-            if (lane >= d) x = df_add(y, x);
-        }
-        DF excl = df_shfl_up(x, 1);
-        if (lane == 0) excl = DF{0.f, 0.f};
-        float MX = warp_max(excl.hi + (excl.lo + bmx));
-        float MN = warp_min(excl.hi + (excl.lo + bmn));
-        MX = fmaxf(MX, 0.f);  // split 0: D = 0
-        MN = fminf(MN, 0.f);
-        const float e = fminf(Tp - MX, Tm + MN);
+        const float e = finish_row(ahi, alo, bmx, bmn, Tp, Tm, lane);
         if (lane == 0) {
             ferr[f] = e;
             best = fminf(best, e);
@@ -301,9 +317,15 @@ int screen_occupancy(const SearchShape &s, int words) {
 
 // ---- shortlist ------------------------------------------------------------------------
 
+// The screened error within which a feature must lie of the smallest one
+// (twice the screening bound, in units of the weight total).
+__device__ __forceinline__ float shortlist_threshold(float m, const RoundState *rs) {
+    return m + kScreenMarginUlps * 5.9604644775390625e-8f * (float)(rs->t_pos + rs->t_neg);
+}
+
 __global__ void __launch_bounds__(256)
-    k_shortlist(int64_t nfeat, RoundState *rs, const float *__restrict__ ferr,
-                const float *__restrict__ bmin, int nbmin, int32_t *__restrict__ cand_ids) {
+    k_shortlist(const JobDesc J, const float *__restrict__ bmin, int nbmin) {
+    RoundState *rs = J.rs;
     if (rs->status != VJB_OK || rs->forced) return;
     __shared__ float red[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -314,25 +336,23 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     m = INFINITY;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fminf(m, red[w]);
-    const double tsum = rs->t_pos + rs->t_neg;
-    const float thr = m + kScreenMarginUlps * 5.9604644775390625e-8f * (float)tsum;
+    const float thr = shortlist_threshold(m, rs);
     if (blockIdx.x == 0 && threadIdx.x == 0) rs->screen_min = m;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + warp * 32; base < nfeat; base += stride) {
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + warp * 32; base < J.nfeat; base += stride) {
         const int64_t f = base + lane;
-        const bool take = f < nfeat && ferr[f] <= thr;
+        const bool take = f < J.nfeat && J.ferr[f] <= thr;
         const uint32_t mask = __ballot_sync(0xffffffffu, take);
         if (!mask) continue;
         int slot0 = 0;
         if (lane == 0) slot0 = atomicAdd(&rs->cand_count, __popc(mask));
         slot0 = __shfl_sync(0xffffffffu, slot0, 0);
-        if (take) cand_ids[slot0 + __popc(mask & ((1u << lane) - 1u))] = (int32_t)f;
+        if (take) J.cand_ids[slot0 + __popc(mask & ((1u << lane) - 1u))] = (int32_t)f;
     }
 }
 
-cudaError_t launch_shortlist(int64_t nfeat, RoundState *rs, const float *ferr, const float *bmin,
-                             int nbmin, int32_t *cand_ids, int grid, cudaStream_t st) {
-    k_shortlist<<<grid, 256, 0, st>>>(nfeat, rs, ferr, bmin, nbmin, cand_ids);
+cudaError_t launch_shortlist(const JobDesc &J, const float *bmin, int nbmin, int grid, cudaStream_t st) {
+    k_shortlist<<<grid, 256, 0, st>>>(J, bmin, nbmin);
     return cudaGetLastError();
 }
 
@@ -437,67 +457,56 @@ __device__ RunResult rescan_run(const uint16_t *__restrict__ row, int run, int k
     return r;
 }
 
-__global__ void __launch_bounds__(kRescanWarps * 32)
-    k_rescan(const uint16_t *__restrict__ rows, int npad, const float *__restrict__ v,
-             RoundState *rs, const int32_t *__restrict__ cand_ids, Candidate *__restrict__ cands) {
-    if (rs->status != VJB_OK || rs->forced) return;
-    __shared__ RunResult rres[32];
-    __shared__ Candidate wc[kRescanWarps];
-    __shared__ bool last_cta;
+// The whole CTA (kRescanWarps warps) re-scans feature f of job J; thread 0
+// returns its best (error, split, polarity).  `rres` is 32 slots of shared memory.
+__device__ Candidate rescan_feature(const JobDesc &J, int32_t f, RunResult *rres) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int cnt = rs->cand_count;
-    const int run = npad / 32;
-    const DF Tp = df_from_double(rs->t_pos), Tm = df_from_double(rs->t_neg);
-    for (int c = blockIdx.x; c < cnt; c += gridDim.x) {
-        const int32_t f = cand_ids[c];
-        const uint16_t *row = rows + (size_t)f * npad;
-        for (int k = warp; k < 32; k += kRescanWarps) {
-            const RunResult r = rescan_run(row, run, k, v, lane);
-            if (lane == 0) rres[k] = r;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            DF offs{0.f, 0.f}, bmax{0.f, 0.f}, bmn{0.f, 0.f};  // split 0: D = 0
-            int smax = 0, smn = 0;
-            for (int k = 0; k < 32; ++k) {  // runs in value order
-                const RunResult &q = rres[k];
-                if (q.smx != INT_MAX) {
-                    const DF cc = df_add(offs, q.mx);
-                    if (df_less(bmax, cc)) { bmax = cc; smax = q.smx; }
-                }
-                if (q.smn != INT_MAX) {
-                    const DF cc = df_add(offs, q.mn);
-                    if (df_less(cc, bmn)) { bmn = cc; smn = q.smn; }
-                }
-                offs = df_add(offs, q.total);
-            }
-            const DF ep = df_add(Tp, df_neg(bmax));
-            const DF em = df_add(Tm, bmn);
-            const bool minus = df_less(em, ep) || (df_eq(em, ep) && smn < smax);
-            Candidate cd;
-            cd.err_hi = minus ? em.hi : ep.hi;
-            cd.err_lo = minus ? em.lo : ep.lo;
-            cd.split = minus ? smn : smax;
-            cd.polarity = minus ? -1 : 1;
-            cd.feature = f;
-            cd.pad = 0;
-            cands[c] = cd;
-        }
-        __syncthreads();
-    }
-    // the last CTA to finish picks the round's stump
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last_cta = atomicAdd(&rs->done_rescan, 1u) == gridDim.x - 1;
+    const int run = J.npad / 32;
+    const uint16_t *row = J.rows + (size_t)f * J.npad;
+    for (int k = warp; k < 32; k += kRescanWarps) {
+        const RunResult r = rescan_run(row, run, k, J.v, lane);
+        if (lane == 0) rres[k] = r;
     }
     __syncthreads();
-    if (!last_cta) return;
-    __threadfence();
+    Candidate cd;
+    cd.err_hi = INFINITY; cd.err_lo = 0.f; cd.feature = f; cd.split = 0; cd.polarity = 1; cd.pad = 0;
+    if (threadIdx.x == 0) {
+        const DF Tp = df_from_double(J.rs->t_pos), Tm = df_from_double(J.rs->t_neg);
+        DF offs{0.f, 0.f}, bmax{0.f, 0.f}, bmn{0.f, 0.f};  // split 0: D = 0
+        int smax = 0, smn = 0;
+        for (int k = 0; k < 32; ++k) {  // runs in value order
+            const RunResult &q = rres[k];
+            if (q.smx != INT_MAX) {
+                const DF cc = df_add(offs, q.mx);
+                if (df_less(bmax, cc)) { bmax = cc; smax = q.smx; }
+            }
+            if (q.smn != INT_MAX) {
+                const DF cc = df_add(offs, q.mn);
+                if (df_less(cc, bmn)) { bmn = cc; smn = q.smn; }
+            }
+            offs = df_add(offs, q.total);
+        }
+        const DF ep = df_add(Tp, df_neg(bmax));
+        const DF em = df_add(Tm, bmn);
+        const bool minus = df_less(em, ep) || (df_eq(em, ep) && smn < smax);
+        cd.err_hi = minus ? em.hi : ep.hi;
+        cd.err_lo = minus ? em.lo : ep.lo;
+        cd.split = minus ? smn : smax;
+        cd.polarity = minus ? -1 : 1;
+    }
+    __syncthreads();
+    return cd;
+}
+
+// The whole CTA picks job J's stump among its `cnt` re-scanned candidates.
+__device__ void select_stump(const JobDesc &J, int cnt) {
+    __shared__ Candidate wc[kRescanWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     Candidate b;
     b.err_hi = INFINITY; b.err_lo = 0.f; b.feature = INT_MAX; b.split = INT_MAX; b.polarity = 1; b.pad = 0;
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
         Candidate c;
-        const volatile Candidate *vc = cands + k;
+        const volatile Candidate *vc = J.cands + k;
         c.err_hi = vc->err_hi; c.err_lo = vc->err_lo; c.feature = vc->feature;
         c.split = vc->split; c.polarity = vc->polarity; c.pad = 0;
         if (cand_less(c, b)) b = c;
@@ -512,6 +521,7 @@ __global__ void __launch_bounds__(kRescanWarps * 32)
     if (threadIdx.x == 0) {
         for (int w = 1; w < kRescanWarps; ++w)
             if (cand_less(wc[w], b)) b = wc[w];
+        RoundState *rs = J.rs;
         if (cnt == 0 || b.feature == INT_MAX) {
             rs->flags |= kFlagNoCandidate;
             rs->status = VJB_EDEVICE;
@@ -524,13 +534,443 @@ __global__ void __launch_bounds__(kRescanWarps * 32)
         }
         rs->done_rescan = 0u;
     }
+    __syncthreads();
 }
 
-cudaError_t launch_rescan(const uint16_t *rows, int npad, const float *v, const WeightLayout &L,
-                          RoundState *rs, const int32_t *cand_ids, Candidate *cands, int grid,
-                          cudaStream_t st) {
-    (void)L;
-    k_rescan<<<grid, kRescanWarps * 32, 0, st>>>(rows, npad, v, rs, cand_ids, cands);
+__global__ void __launch_bounds__(kRescanWarps * 32) k_rescan(const JobDesc J) {
+    if (J.rs->status != VJB_OK || J.rs->forced) return;
+    __shared__ RunResult rres[32];
+    __shared__ bool last_cta;
+    const int cnt = J.rs->cand_count;
+    for (int c = blockIdx.x; c < cnt; c += gridDim.x) {
+        const Candidate cd = rescan_feature(J, J.cand_ids[c], rres);
+        if (threadIdx.x == 0) J.cands[c] = cd;
+    }
+    // the last CTA to finish picks the round's stump
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last_cta = atomicAdd(&J.rs->done_rescan, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last_cta) return;
+    __threadfence();
+    select_stump(J, cnt);
+}
+
+cudaError_t launch_rescan(const JobDesc &J, int grid, cudaStream_t st) {
+    k_rescan<<<grid, kRescanWarps * 32, 0, st>>>(J);
+    return cudaGetLastError();
+}
+
+// ---- batched rounds --------------------------------------------------------------------
+// A batch trains many jobs at once: one launch of each round kernel covers all
+// of them.  The job table and the counters live in device memory, so a round
+// replays as one CUDA graph however the set of jobs changes between rounds.
+
+// Which jobs take part in this round; per-job search minimum reset.
+__global__ void k_bbegin(JobDesc *jobs, BatchMeta *meta) {
+    const int nj = meta->njobs;
+    for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+        RoundState *rs = jobs[j].rs;
+        const int in = jobs[j].active && rs->status == VJB_OK && rs->forced == 0 &&
+                       rs->rounds < jobs[j].round_target;
+        rs->in_round = in;
+        rs->screen_min_bits = 0x7f800000u;  // +inf
+    }
+}
+
+cudaError_t launch_bbegin(JobDesc *jobs, BatchMeta *meta, cudaStream_t st) {
+    k_bbegin<<<1, 256, 0, st>>>(jobs, meta);
+    return cudaGetLastError();
+}
+
+size_t bscreen_smem_bytes(const SearchShape &s, int max_words) {
+    SearchShape t = s;
+    t.box_lines = kBoxLinesMax;  // batch stages always hold a whole 32-line chunk
+    return search_smem_bytes(t, max_words);
+}
+
+// Loads `lines_here` lines (a multiple of 4, at most 32) at `line` of the
+// arena into a stage, as boxes of 32, 16, 8 and 4 lines, all completing on `bar`.
+__device__ __forceinline__ void load_lines(const BatchMaps &maps, uint32_t dst, int64_t line,
+                                           int lines_here, uint32_t bar) {
+    mbar_arrive_expect_tx(bar, (uint32_t)lines_here * kLineBytes);
+    int done = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int box = kBoxLinesMax >> b;
+        if (lines_here - done >= box) {
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst + (uint32_t)done * kLineBytes),
+                "l"(reinterpret_cast<uint64_t>(&maps.m[b])), "r"(0), "r"((int32_t)(line + done)), "r"(bar)
+                : "memory");
+            done += box;
+        }
+    }
+}
+
+template <int U>
+__global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
+    k_bscreen(const __grid_constant__ BatchMaps maps, const JobDesc *__restrict__ jobs,
+              const WorkItem *__restrict__ items, BatchMeta *meta, int max_words, int stages) {
+    extern __shared__ __align__(16) float sv[];
+    __shared__ int s_item;
+    __shared__ float s_min[32];
+    const int nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t stage_bytes = kStageBytes;
+    const uint32_t sv32 = smem_u32(sv);
+    const uint32_t ring0 = (uint32_t)align_up(sv32 + (uint32_t)max_words * 4u, 1024);
+    const uint32_t bars0 = ring0 + (uint32_t)nw * stages * stage_bytes;
+    const uint32_t ring_w = ring0 + (uint32_t)warp * stages * stage_bytes;
+    const uint32_t bar_w = bars0 + (uint32_t)(warp * stages * 8);
+    if (lane == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(bar_w + 8 * s, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    const int n_items = meta->n_items;
+    int cur_job = -1;
+    int pstage = 0, cstage = 0;
+    uint32_t cpar = 0;
+    bool ok = true;  // false once one of this warp's waits timed out
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(&meta->item_next, 1u);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const WorkItem W = items[it];
+        const JobDesc &J = jobs[W.job];
+        if (!J.rs->in_round) continue;
+        if (W.job != cur_job) {  // this job's weights into shared memory
+            for (int i = threadIdx.x; i < J.lay.words; i += blockDim.x) sv[i] = J.v[i];
+            __syncthreads();
+            cur_job = W.job;
+        }
+        const int lines = J.lines;
+        const int nc = (lines + kBoxLinesMax - 1) / kBoxLinesMax;
+        const int nrows = W.f1 - W.f0 > warp ? (W.f1 - W.f0 - warp + nw - 1) / nw : 0;
+        const int total = ok ? nrows * nc : 0;
+        const float Tp = (float)J.rs->t_pos, Tm = (float)J.rs->t_neg;
+        // producer (lane 0) position inside this item
+        int pk = 0, pc = 0, issued = 0;
+        auto issue_next = [&]() {
+            if (issued >= total) return;
+            const int64_t f = W.f0 + warp + (int64_t)pk * nw;
+            const int lh = min(kBoxLinesMax, lines - pc * kBoxLinesMax);
+            load_lines(maps, ring_w + (uint32_t)pstage * stage_bytes,
+                       J.line_base + f * lines + (int64_t)pc * kBoxLinesMax, lh, bar_w + 8u * (uint32_t)pstage);
+            if (++pc == nc) { pc = 0; ++pk; }
+            if (++pstage == stages) pstage = 0;
+            ++issued;
+        };
+        if (lane == 0)
+            for (int s = 0; s < stages; ++s) issue_next();
+        __syncwarp();
+        float wmin = INFINITY;
+        int consumed = 0;
+        for (int k = 0; k < nrows && ok; ++k) {
+            const int64_t f = W.f0 + warp + (int64_t)k * nw;
+            float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
+            for (int c = 0; c < nc; ++c) {
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
+                    ok = false;
+                    break;
+                }
+                const int lh = min(kBoxLinesMax, lines - c * kBoxLinesMax);
+                scan_stage<U>(ring_w + (uint32_t)cstage * stage_bytes, lh >> 2, lane, sv, ahi, alo, bmx, bmn);
+                __syncwarp();
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    issue_next();
+                }
+                if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
+                ++consumed;
+            }
+            if (!ok) break;
+            const float e = finish_row(ahi, alo, bmx, bmn, Tp, Tm, lane);
+            if (lane == 0) J.ferr[f] = e;
+            wmin = fminf(wmin, e);
+        }
+        if (!ok) {
+            // record the failure, wait (bounded) for this warp's copies in flight, stop working
+            if (lane == 0) {
+                atomicOr(&meta->flags, kFlagWaitTimeout);
+                atomicOr(&J.rs->flags, kFlagWaitTimeout);
+                const int pending = __shfl_sync(1u, issued, 0) - consumed;
+                for (int s = 0; s < pending; ++s) {
+                    mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar, 100000000ull);
+                    if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
+                }
+            }
+            __syncwarp();
+        }
+        if (lane == 0) s_min[warp] = wmin;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float m = INFINITY;
+            for (int w = 0; w < nw; ++w) m = fminf(m, s_min[w]);
+            if (m < INFINITY) atomicMin(&J.rs->screen_min_bits, __float_as_uint(fmaxf(m, 0.f)));
+        }
+        __syncthreads();
+    }
+    // the last CTA resets the work queue for the next round
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&meta->screen_done, 1u) == gridDim.x - 1) {
+            meta->item_next = 0u;
+            meta->screen_done = 0u;
+        }
+    }
+}
+
+// Interleaved schedule: the plain kernel's row order applied to every job in
+// turn.  Warp w of the grid takes rows w, w + G, w + 2G, ... (G warps in the
+// grid) of job 0, then of job 1, and so on; its producer lane runs ahead
+// across job boundaries, so the TMA ring never drains.  The CTA synchronises
+// only when it moves to the next job (to swap the weights in shared memory),
+// and skips jobs in which none of its warps has a row.
+template <int U>
+__global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
+    k_bscreen_il(const __grid_constant__ BatchMaps maps, const JobDesc *__restrict__ jobs,
+                 BatchMeta *meta, int max_words, int stages) {
+    extern __shared__ __align__(16) float sv[];
+    __shared__ float s_min[32];
+    const int nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t stage_bytes = kStageBytes;
+    const uint32_t sv32 = smem_u32(sv);
+    const uint32_t ring0 = (uint32_t)align_up(sv32 + (uint32_t)max_words * 4u, 1024);
+    const uint32_t bars0 = ring0 + (uint32_t)nw * stages * stage_bytes;
+    const uint32_t ring_w = ring0 + (uint32_t)warp * stages * stage_bytes;
+    const uint32_t bar_w = bars0 + (uint32_t)(warp * stages * 8);
+    if (lane == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(bar_w + 8 * s, 1);
+        fence_barrier_init();
+    }
+    const int nj = meta->njobs;
+    const int64_t gw = (int64_t)blockIdx.x * nw + warp;
+    const int64_t G = (int64_t)gridDim.x * nw;
+    auto rows_of = [&](const JobDesc &J) -> int64_t {
+        return (J.rs->in_round && gw < J.nfeat) ? (J.nfeat - 1 - gw) / G + 1 : 0;
+    };
+    // producer (lane 0): job, row and chunk of the next load, in this warp's order
+    int pj = -1, pc = 0, pstage = 0, p_nc = 0, p_lines = 0;
+    int64_t pk = 0, p_rows = 0, p_base = 0, issued = 0;
+    auto next_job = [&]() {
+        for (++pj; pj < nj; ++pj) {
+            const JobDesc &J = jobs[pj];
+            p_rows = rows_of(J);
+            if (p_rows) {
+                p_lines = J.lines;
+                p_nc = (p_lines + kBoxLinesMax - 1) / kBoxLinesMax;
+                p_base = J.line_base;
+                pk = 0;
+                pc = 0;
+                return;
+            }
+        }
+    };
+    auto issue_next = [&]() {
+        if (pj >= nj) return;
+        const int lh = min(kBoxLinesMax, p_lines - pc * kBoxLinesMax);
+        load_lines(maps, ring_w + (uint32_t)pstage * stage_bytes,
+                   p_base + (gw + pk * G) * p_lines + (int64_t)pc * kBoxLinesMax, lh, bar_w + 8u * (uint32_t)pstage);
+        if (++pstage == stages) pstage = 0;
+        ++issued;
+        if (++pc == p_nc) {
+            pc = 0;
+            if (++pk == p_rows) next_job();
+        }
+    };
+    if (lane == 0) {
+        next_job();
+        for (int s = 0; s < stages; ++s) issue_next();
+    }
+    __syncwarp();
+    int cstage = 0, prev = -1;
+    uint32_t cpar = 0;
+    int64_t consumed = 0;
+    bool ok = true;  // false once one of this warp's waits timed out
+    for (int j = 0; j < nj; ++j) {
+        const JobDesc &J = jobs[j];
+        if (!J.rs->in_round || (int64_t)blockIdx.x * nw >= J.nfeat) continue;  // uniform over the CTA
+        __syncthreads();  // every warp is done with the previous job's weights and minima
+        if (prev >= 0 && threadIdx.x == 0) {
+            float m = INFINITY;
+            for (int w = 0; w < nw; ++w) m = fminf(m, s_min[w]);
+            if (m < INFINITY) atomicMin(&jobs[prev].rs->screen_min_bits, __float_as_uint(fmaxf(m, 0.f)));
+        }
+        for (int i = threadIdx.x; i < J.lay.words; i += blockDim.x) sv[i] = J.v[i];
+        __syncthreads();
+        prev = j;
+        const int lines = J.lines;
+        const int nc = (lines + kBoxLinesMax - 1) / kBoxLinesMax;
+        const int64_t nrows = ok ? rows_of(J) : 0;
+        const float Tp = (float)J.rs->t_pos, Tm = (float)J.rs->t_neg;
+        float wmin = INFINITY;
+        for (int64_t k = 0; k < nrows && ok; ++k) {
+            const int64_t f = gw + k * G;
+            float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
+            for (int c = 0; c < nc; ++c) {
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
+                    ok = false;
+                    break;
+                }
+                const int lh = min(kBoxLinesMax, lines - c * kBoxLinesMax);
+                scan_stage<U>(ring_w + (uint32_t)cstage * stage_bytes, lh >> 2, lane, sv, ahi, alo, bmx, bmn);
+                __syncwarp();
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    issue_next();
+                }
+                if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
+                ++consumed;
+            }
+            if (!ok) break;
+            const float e = finish_row(ahi, alo, bmx, bmn, Tp, Tm, lane);
+            if (lane == 0) J.ferr[f] = e;
+            wmin = fminf(wmin, e);
+        }
+        if (!ok && lane == 0) {
+            atomicOr(&meta->flags, kFlagWaitTimeout);
+            atomicOr(&J.rs->flags, kFlagWaitTimeout);
+        }
+        if (lane == 0) s_min[warp] = wmin;
+    }
+    __syncthreads();
+    if (prev >= 0 && threadIdx.x == 0) {
+        float m = INFINITY;
+        for (int w = 0; w < nw; ++w) m = fminf(m, s_min[w]);
+        if (m < INFINITY) atomicMin(&jobs[prev].rs->screen_min_bits, __float_as_uint(fmaxf(m, 0.f)));
+    }
+    if (!ok && lane == 0) {
+        // wait (bounded) for this warp's copies still in flight before the CTA exits
+        const int64_t pending = issued - consumed;
+        for (int64_t s = 0; s < pending; ++s) {
+            mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar, 100000000ull);
+            if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
+        }
+    }
+}
+
+cudaError_t launch_bscreen(const BatchMaps &maps, const JobDesc *jobs, const WorkItem *items,
+                           BatchMeta *meta, int max_words, const SearchShape &shape, bool interleaved,
+                           int grid, cudaStream_t st) {
+    const size_t sm = bscreen_smem_bytes(shape, max_words);
+    const int threads = shape.warps * 32;
+    if (interleaved) {
+        switch (shape.unroll) {
+        case 1: k_bscreen_il<1><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages); break;
+        case 4: k_bscreen_il<4><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages); break;
+        default: k_bscreen_il<2><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages);
+        }
+        return cudaGetLastError();
+    }
+    switch (shape.unroll) {
+    case 1: k_bscreen<1><<<grid, threads, sm, st>>>(maps, jobs, items, meta, max_words, shape.stages); break;
+    case 4: k_bscreen<4><<<grid, threads, sm, st>>>(maps, jobs, items, meta, max_words, shape.stages); break;
+    default: k_bscreen<2><<<grid, threads, sm, st>>>(maps, jobs, items, meta, max_words, shape.stages);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t set_bscreen_smem_limit(int bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_bscreen<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bscreen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bscreen<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bscreen_il<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bscreen_il<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bscreen_il<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+// Index of the job whose range [base_j, base_{j+1}) holds g (bases ascending).
+template <class F>
+__device__ __forceinline__ int find_job(int nj, int64_t g, F base) {
+    int lo = 0, hi = nj - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base(mid) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_bshortlist(const JobDesc *__restrict__ jobs, BatchMeta *meta) {
+    __shared__ int64_t base[kMaxBatchJobs];
+    const int nj = meta->njobs;
+    const int64_t total = meta->total_feat;
+    for (int j = threadIdx.x; j < nj; j += blockDim.x) base[j] = jobs[j].feat_base;
+    __syncthreads();
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < nj; j += blockDim.x)
+            if (jobs[j].rs->in_round) jobs[j].rs->screen_min = __uint_as_float(jobs[j].rs->screen_min_bits);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+        const int j = find_job(nj, g, [&](int i) { return base[i]; });
+        const JobDesc &J = jobs[j];
+        RoundState *rs = J.rs;
+        if (!rs->in_round) continue;
+        const int64_t f = g - J.feat_base;
+        if (f >= J.nfeat) continue;
+        const float thr = shortlist_threshold(__uint_as_float(rs->screen_min_bits), rs);
+        if (J.ferr[f] <= thr) J.cand_ids[atomicAdd(&rs->cand_count, 1)] = (int32_t)f;
+    }
+}
+
+cudaError_t launch_bshortlist(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st) {
+    k_bshortlist<<<grid, 256, 0, st>>>(jobs, meta);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kRescanWarps * 32) k_brescan(const JobDesc *__restrict__ jobs, BatchMeta *meta) {
+    __shared__ RunResult rres[32];
+    __shared__ int pref[kMaxBatchJobs + 1];
+    __shared__ bool s_last;
+    const int nj = meta->njobs;
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int j = 0; j < nj; ++j) {
+            pref[j] = acc;
+            const RoundState *rs = jobs[j].rs;
+            if (rs->in_round && rs->status == VJB_OK) {
+                if (rs->cand_count == 0 && blockIdx.x == 0) {  // nothing to pick from: stop the job
+                    jobs[j].rs->flags |= kFlagNoCandidate;
+                    jobs[j].rs->status = VJB_EDEVICE;
+                } else {
+                    acc += rs->cand_count;
+                }
+            }
+        }
+        pref[nj] = acc;
+    }
+    __syncthreads();
+    const int total = pref[nj];
+    for (int p = blockIdx.x; p < total; p += gridDim.x) {
+        int j = 0;
+        while (pref[j + 1] <= p) ++j;
+        const JobDesc &J = jobs[j];
+        const int c = p - pref[j];
+        const Candidate cd = rescan_feature(J, J.cand_ids[c], rres);
+        if (threadIdx.x == 0) {
+            J.cands[c] = cd;
+            __threadfence();
+            s_last = atomicAdd(&J.rs->done_rescan, 1u) == (uint32_t)(pref[j + 1] - pref[j]) - 1;
+        }
+        __syncthreads();
+        if (s_last) {  // the job's last candidate: pick its stump
+            __threadfence();
+            select_stump(J, pref[j + 1] - pref[j]);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_brescan(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st) {
+    k_brescan<<<grid, kRescanWarps * 32, 0, st>>>(jobs, meta);
     return cudaGetLastError();
 }
 

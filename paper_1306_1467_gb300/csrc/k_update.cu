@@ -79,6 +79,8 @@ __global__ void __launch_bounds__(kOneCta)
         rs->cand_count = 0;
         rs->forced = 0;
         rs->done_rescan = rs->done_update_a = rs->done_update_b = 0u;
+        rs->screen_min_bits = 0x7f800000u;
+        rs->in_round = 0;
         if (!(tot > 0.0) || !isfinite(tot)) rs->flags |= kFlagBadWeights;
     }
 }
@@ -94,8 +96,8 @@ int update_grid(int n) {
     return g < 1 ? 1 : (g > kUpdateMaxCtas ? kUpdateMaxCtas : g);
 }
 
-// Per-CTA reduction of three doubles into partials[3 * blockIdx.x + k].
-__device__ __forceinline__ void cta_partials(double a, double b, double c, double *partials) {
+// Per-CTA reduction of three doubles into partials[3 * blk + k].
+__device__ __forceinline__ void cta_partials(double a, double b, double c, double *partials, int blk) {
     __shared__ double red[3][kUpdateThreads / 32];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     a = warp_sum_d(a);
@@ -106,82 +108,91 @@ __device__ __forceinline__ void cta_partials(double a, double b, double c, doubl
     if (threadIdx.x == 0) {
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
         for (int k = 0; k < kUpdateThreads / 32; ++k) { s0 += red[0][k]; s1 += red[1][k]; s2 += red[2][k]; }
-        partials[3 * blockIdx.x + 0] = s0;
-        partials[3 * blockIdx.x + 1] = s1;
-        partials[3 * blockIdx.x + 2] = s2;
+        partials[3 * blk + 0] = s0;
+        partials[3 * blk + 1] = s1;
+        partials[3 * blk + 2] = s2;
     }
 }
 
-// True in the one CTA that finishes last (thread 0 decides, all threads learn).
-__device__ __forceinline__ bool last_cta_done(uint32_t *counter) {
+// True in the CTA that finishes the last of `nblocks` blocks counted on
+// `counter` (thread 0 decides, all threads learn).
+__device__ __forceinline__ bool last_block_done(uint32_t *counter, int nblocks) {
     __shared__ bool last;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+        last = atomicAdd(counter, 1u) == (uint32_t)nblocks - 1;
     }
     __syncthreads();
     if (last) __threadfence();
     return last;
 }
 
-__global__ void __launch_bounds__(kUpdateThreads)
-    k_update_a(const uint16_t *__restrict__ rows, int npad, WeightLayout L,
-               const int32_t *__restrict__ ii_t, int ii_stride, int w, const DevFeature *__restrict__ feat,
-               const uint8_t *__restrict__ y, const float *__restrict__ wts, uint8_t *__restrict__ miss,
-               double *partials, RoundState *rs, vjb_stump *stumps, vjb_round_diag *diag,
-               int stump_cap, vjb_stump *last, const float *__restrict__ ferr) {
-    if (rs->status != VJB_OK) return;
-    const int n = L.n;
+// Step 3-4, part 1, for the 256 samples (or sorted positions) of block `blk`:
+// e_i and the block's FP64 sums of misclassified weight, of all weight and (for
+// a host-given stump) of samples below the threshold.
+__device__ void update_a_block(const JobDesc &J, int blk) {
+    const int n = J.lay.n;
+    const RoundState *rs = J.rs;
     const bool forced = rs->forced != 0;
     const int32_t f = forced ? rs->forced_feature : rs->win_feature;
     const int32_t p = forced ? rs->forced_polarity : rs->win_polarity;
     const int32_t s = forced ? 0 : rs->win_split;
     const int32_t theta_f = rs->forced_threshold;
-    const DevFeature d = feat[f];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blk * kUpdateThreads + threadIdx.x;
     double mw = 0.0, tw = 0.0, below = 0.0;
     if (k < n) {
         int i;
         bool h;
         if (!forced) {
             // sorted position k: the first s positions are "below" the threshold
-            i = word_to_sample(rows[(size_t)f * npad + phys_of(k, npad / 32)] & kIndexMask, L);
+            i = word_to_sample(J.rows[(size_t)f * J.npad + phys_of(k, J.npad / 32)] & kIndexMask, J.lay);
             const bool bl = k < s;
             h = (p > 0) ? bl : !bl;
         } else {
             i = k;
-            const int32_t val = haar_value(ii_t, ii_stride, w, d.type, d.x, d.y, d.w, d.h, i);
+            const DevFeature d = J.feat[f];
+            const int32_t val = haar_value(J.ii, J.ii_stride, J.win_w, d.type, d.x, d.y, d.w, d.h, i);
             h = (p > 0) ? (val < theta_f) : (val > theta_f);
             below = (p > 0) ? (val < theta_f) : (val <= theta_f);
         }
-        const bool m = h != (y[i] != 0);
-        miss[i] = m;
-        const double wi = (double)wts[i];
+        const bool m = h != (J.y[i] != 0);
+        J.miss[i] = m;
+        const double wi = (double)J.w[i];
         tw = wi;
         if (m) mw = wi;
     }
-    cta_partials(mw, tw, below, partials);
-    if (!last_cta_done(&rs->done_update_a)) return;
-    if (threadIdx.x != 0) return;
+    cta_partials(mw, tw, below, J.partials, blk);
+}
+
+// Step 3-4, part 1, finish (one thread, after every block): the stump's FP64
+// error, threshold, beta and alpha, its record, and the update factors.
+__device__ void update_a_finish(const JobDesc &J, int nblocks) {
+    RoundState *rs = J.rs;
+    const int n = J.lay.n;
+    const bool forced = rs->forced != 0;
+    const int32_t f = forced ? rs->forced_feature : rs->win_feature;
+    const int32_t p = forced ? rs->forced_polarity : rs->win_polarity;
+    const int32_t s = forced ? 0 : rs->win_split;
+    const DevFeature d = J.feat[f];
     double M = 0.0, T = 0.0, B = 0.0;
-    for (unsigned c = 0; c < gridDim.x; ++c) {
-        M += ((volatile double *)partials)[3 * c + 0];
-        T += ((volatile double *)partials)[3 * c + 1];
-        B += ((volatile double *)partials)[3 * c + 2];
+    for (int c = 0; c < nblocks; ++c) {
+        M += ((volatile double *)J.partials)[3 * c + 0];
+        T += ((volatile double *)J.partials)[3 * c + 1];
+        B += ((volatile double *)J.partials)[3 * c + 2];
     }
     const double eps = M / T;
     int32_t theta, split = s;
     if (forced) {
-        theta = theta_f;
+        theta = rs->forced_threshold;
         split = (int32_t)B;
     } else {
         // canonical threshold: p=+1 -> value at position s (max+1 at s = n);
         // p=-1 -> value at position s-1 (min-1 at s = 0)
-        const uint16_t *row = rows + (size_t)f * npad;
+        const uint16_t *row = J.rows + (size_t)f * J.npad;
         auto val_at = [&](int pos) {
-            const int i = word_to_sample(row[phys_of(pos, npad / 32)] & kIndexMask, L);
-            return haar_value(ii_t, ii_stride, w, d.type, d.x, d.y, d.w, d.h, i);
+            const int i = word_to_sample(row[phys_of(pos, J.npad / 32)] & kIndexMask, J.lay);
+            return haar_value(J.ii, J.ii_stride, J.win_w, d.type, d.x, d.y, d.w, d.h, i);
         };
         if (p > 0) theta = (s < n) ? val_at(s) : val_at(n - 1) + 1;
         else theta = (s > 0) ? val_at(s - 1) : val_at(0) - 1;
@@ -196,11 +207,11 @@ __global__ void __launch_bounds__(kUpdateThreads)
     // works in units of the current weight total T, so divide by it
     vjb_round_diag dg;
     dg.search_error = forced ? eps : ((double)rs->win_err_hi + (double)rs->win_err_lo) / T;
-    dg.screen_error = forced ? (float)eps : (float)((double)ferr[f] / T);
+    dg.screen_error = forced ? (float)eps : (float)((double)J.ferr[f] / T);
     dg.screen_min = forced ? (float)eps : (float)((double)rs->screen_min / T);
     dg.candidates = forced ? 0 : rs->cand_count;
     dg.forced = forced ? 1 : 0;
-    if (rs->rounds < stump_cap) diag[rs->rounds] = dg;
+    if (rs->rounds < J.stump_cap) J.diag[rs->rounds] = dg;
     rs->last_cands = rs->cand_count;
     rs->cand_count = 0;
     rs->forced = 0;
@@ -209,51 +220,49 @@ __global__ void __launch_bounds__(kUpdateThreads)
         // perfect stump: kept with alpha = +inf, training is over
         st.beta = 0.0;
         st.alpha = INFINITY;
-        if (rs->rounds < stump_cap) stumps[rs->rounds] = st;
+        if (rs->rounds < J.stump_cap) J.stumps[rs->rounds] = st;
         rs->rounds += 1;
-        *last = st;
+        *J.last = st;
         rs->status = VJB_DONE_PERFECT;
         return;
     }
     const double beta = eps / (1.0 - eps);
     st.beta = beta;
     st.alpha = log((1.0 - eps) / eps);  // log(1 / beta)
-    *last = st;
+    *J.last = st;
     if (eps >= 0.5) {
         // no stump does better than chance: not kept, training is over
         rs->status = VJB_DONE_NOGAIN;
         return;
     }
-    if (rs->rounds < stump_cap) stumps[rs->rounds] = st;
+    if (rs->rounds < J.stump_cap) J.stumps[rs->rounds] = st;
     rs->rounds += 1;
     const double Z = M + beta * (T - M);
     rs->scale_hit = beta / Z;
     rs->scale_miss = 1.0 / Z;
 }
 
-__global__ void __launch_bounds__(kUpdateThreads)
-    k_update_b(WeightLayout L, const uint8_t *__restrict__ y, float *__restrict__ wts,
-               float *__restrict__ v, const uint8_t *__restrict__ miss, double *partials,
-               RoundState *rs) {
-    if (rs->status != VJB_OK) return;
-    const int n = L.n;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Step 4 and step 1 of the next round for the 256 samples of block `blk`.
+__device__ void update_b_block(const JobDesc &J, int blk) {
+    const int i = blk * kUpdateThreads + threadIdx.x;
     double tp = 0.0, tn = 0.0;
-    if (i < n) {
-        const double scale = miss[i] ? rs->scale_miss : rs->scale_hit;
-        const float fw = __double2float_rn((double)wts[i] * scale);
-        wts[i] = fw;
-        const bool face = y[i] != 0;
-        store_v(v, L, i, face ? fw : -fw);
+    if (i < J.lay.n) {
+        const double scale = J.miss[i] ? J.rs->scale_miss : J.rs->scale_hit;
+        const float fw = __double2float_rn((double)J.w[i] * scale);
+        J.w[i] = fw;
+        const bool face = J.y[i] != 0;
+        store_v(J.v, J.lay, i, face ? fw : -fw);
         if (face) tp = (double)fw; else tn = (double)fw;
     }
-    cta_partials(tp, tn, 0.0, partials);
-    if (!last_cta_done(&rs->done_update_b)) return;
-    if (threadIdx.x != 0) return;
+    cta_partials(tp, tn, 0.0, J.partials, blk);
+}
+
+__device__ void update_b_finish(const JobDesc &J, int nblocks) {
+    RoundState *rs = J.rs;
     double P = 0.0, Q = 0.0;
-    for (unsigned c = 0; c < gridDim.x; ++c) {
-        P += ((volatile double *)partials)[3 * c + 0];
-        Q += ((volatile double *)partials)[3 * c + 1];
+    for (int c = 0; c < nblocks; ++c) {
+        P += ((volatile double *)J.partials)[3 * c + 0];
+        Q += ((volatile double *)J.partials)[3 * c + 1];
     }
     rs->t_pos = P;
     rs->t_neg = Q;
@@ -261,21 +270,69 @@ __global__ void __launch_bounds__(kUpdateThreads)
     rs->done_update_b = 0u;
 }
 
-cudaError_t launch_update_a(const uint16_t *rows, int npad, const WeightLayout &L,
-                            const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
-                            const uint8_t *y, const float *wts, uint8_t *miss, double *partials,
-                            RoundState *rs, vjb_stump *stumps, vjb_round_diag *diag, int stump_cap,
-                            vjb_stump *last, const float *ferr, cudaStream_t st) {
-    k_update_a<<<update_grid(L.n), kUpdateThreads, 0, st>>>(rows, npad, L, ii_t, ii_stride, w, feat, y,
-                                                            wts, miss, partials, rs, stumps, diag,
-                                                            stump_cap, last, ferr);
+__global__ void __launch_bounds__(kUpdateThreads) k_update_a(const JobDesc J) {
+    if (J.rs->status != VJB_OK) return;
+    update_a_block(J, blockIdx.x);
+    if (!last_block_done(&J.rs->done_update_a, gridDim.x)) return;
+    if (threadIdx.x == 0) update_a_finish(J, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kUpdateThreads) k_update_b(const JobDesc J) {
+    if (J.rs->status != VJB_OK) return;
+    update_b_block(J, blockIdx.x);
+    if (!last_block_done(&J.rs->done_update_b, gridDim.x)) return;
+    if (threadIdx.x == 0) update_b_finish(J, gridDim.x);
+}
+
+cudaError_t launch_update_a(const JobDesc &J, cudaStream_t st) {
+    k_update_a<<<update_grid(J.lay.n), kUpdateThreads, 0, st>>>(J);
     return cudaGetLastError();
 }
 
-cudaError_t launch_update_b(const WeightLayout &L, const uint8_t *y, float *wts, float *v,
-                            const uint8_t *miss, double *partials, RoundState *rs,
-                            cudaStream_t st) {
-    k_update_b<<<update_grid(L.n), kUpdateThreads, 0, st>>>(L, y, wts, v, miss, partials, rs);
+cudaError_t launch_update_b(const JobDesc &J, cudaStream_t st) {
+    k_update_b<<<update_grid(J.lay.n), kUpdateThreads, 0, st>>>(J);
+    return cudaGetLastError();
+}
+
+// Batched: the blocks of all jobs in the round, flattened (job j owns blocks
+// [ublock_base_j, ublock_base_j + update_grid(n_j))), each job's last block
+// finishing it.  The same blocks and the same order of partial sums as the
+// plain kernels, so a job's results do not depend on its batch.
+template <bool A>
+__global__ void __launch_bounds__(kUpdateThreads) k_bupdate(const JobDesc *__restrict__ jobs, BatchMeta *meta) {
+    __shared__ int base[kMaxBatchJobs + 1];
+    const int nj = meta->njobs;
+    for (int j = threadIdx.x; j < nj; j += blockDim.x) base[j] = jobs[j].ublock_base;
+    if (threadIdx.x == 0) base[nj] = meta->total_ublocks;
+    __syncthreads();
+    const int total = base[nj];
+    for (int g = blockIdx.x; g < total; g += gridDim.x) {
+        int lo = 0, hi = nj - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (base[mid] <= g) lo = mid;
+            else hi = mid - 1;
+        }
+        const JobDesc &J = jobs[lo];
+        const int blk = g - base[lo], nblocks = base[lo + 1] - base[lo];
+        if (!J.rs->in_round || J.rs->status != VJB_OK) continue;
+        if (A) update_a_block(J, blk);
+        else update_b_block(J, blk);
+        if (last_block_done(A ? &J.rs->done_update_a : &J.rs->done_update_b, nblocks) && threadIdx.x == 0) {
+            if (A) update_a_finish(J, nblocks);
+            else update_b_finish(J, nblocks);
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_bupdate_a(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st) {
+    k_bupdate<true><<<grid, kUpdateThreads, 0, st>>>(jobs, meta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bupdate_b(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st) {
+    k_bupdate<false><<<grid, kUpdateThreads, 0, st>>>(jobs, meta);
     return cudaGetLastError();
 }
 

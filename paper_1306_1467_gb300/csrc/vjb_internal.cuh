@@ -59,7 +59,8 @@ struct RoundState {
     int32_t win_feature, win_split, win_polarity;  // the round's stump
     uint32_t done_rescan, done_update_a, done_update_b;  // last-CTA counters
     float win_err_hi, win_err_lo;  // the stump's error from the compensated re-scan
-    int32_t pad;
+    uint32_t screen_min_bits;  // batched search: smallest screened error (bits of a float >= 0)
+    int32_t in_round;          // batched rounds: 1 if the job takes part in the current round
 };
 
 // Device error flags.
@@ -114,6 +115,55 @@ constexpr float kScreenMarginUlps = 64.0f;
 constexpr int kUpdateThreads = 256;
 constexpr int kUpdateMaxCtas = 4096;
 
+// Everything the round kernels need about one training job.  The plain
+// kernels get it by value; a batch keeps one per job in device memory.
+struct JobDesc {
+    const uint16_t *rows;  // sorted table [nfeat][npad], lane-run layout
+    int npad, lines;       // row length in entries and in 128-byte lines
+    int64_t nfeat;
+    int64_t line_base;     // batch: first line of the table in the batch's table arena
+    WeightLayout lay;
+    float *v;              // signed weights, lay.words floats
+    float *w;              // FP32 weights [n]
+    const uint8_t *y;
+    uint8_t *miss;
+    double *partials;      // 3 * kUpdateMaxCtas
+    RoundState *rs;
+    float *ferr;
+    int32_t *cand_ids;
+    struct Candidate *cands;
+    vjb_stump *stumps;
+    vjb_round_diag *diag;
+    vjb_stump *last;
+    int32_t stump_cap;
+    int32_t ii_stride;
+    const int32_t *ii;
+    const DevFeature *feat;
+    int32_t win_w;         // window width
+    int32_t active;        // batch: 1 if the job is trained by the batch
+    int32_t round_target;  // batch: train while rounds < round_target
+    int32_t ublock_base;   // batch: update blocks of the jobs before this one
+    int64_t feat_base;     // batch: features of the jobs before this one
+};
+
+// Batch-wide counters in device memory.
+struct BatchMeta {
+    int32_t njobs;          // job slots in use
+    int32_t n_items;        // search work items
+    uint32_t item_next;     // next work item (reset by the last CTA of the search)
+    uint32_t screen_done;   // CTAs done with the search
+    int64_t total_feat;     // sum of nfeat over the job slots
+    int32_t total_ublocks;  // sum of update blocks over the job slots
+    int32_t flags;          // error flags of batched kernels
+};
+
+// A search work item: features [f0, f1) of one job.
+struct WorkItem {
+    int32_t job, f0, f1, pad;
+};
+
+constexpr int kMaxBatchJobs = 256;
+
 struct SearchShape {
     int warps;        // consumer warps per CTA
     int stages;       // TMA stages per warp
@@ -141,19 +191,24 @@ cudaError_t launch_init_weights(const uint8_t *y, const WeightLayout &L, const f
 cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, const WeightLayout &L,
                           int lines_per_row, int box_lines, int64_t nfeat, const SearchShape &shape,
                           int grid, RoundState *rs, float *ferr, float *bmin, cudaStream_t st);
-cudaError_t launch_shortlist(int64_t nfeat, RoundState *rs, const float *ferr, const float *bmin,
-                             int nbmin, int32_t *cand_ids, int grid, cudaStream_t st);
-cudaError_t launch_rescan(const uint16_t *rows, int npad, const float *v, const WeightLayout &L,
-                          RoundState *rs, const int32_t *cand_ids, Candidate *cands, int grid,
-                          cudaStream_t st);
-cudaError_t launch_update_a(const uint16_t *rows, int npad, const WeightLayout &L,
-                            const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
-                            const uint8_t *y, const float *wts, uint8_t *miss, double *partials,
-                            RoundState *rs, vjb_stump *stumps, vjb_round_diag *diag, int stump_cap,
-                            vjb_stump *last, const float *ferr, cudaStream_t st);
-cudaError_t launch_update_b(const WeightLayout &L, const uint8_t *y, float *wts, float *v,
-                            const uint8_t *miss, double *partials, RoundState *rs,
-                            cudaStream_t st);
+cudaError_t launch_shortlist(const JobDesc &J, const float *bmin, int nbmin, int grid, cudaStream_t st);
+cudaError_t launch_rescan(const JobDesc &J, int grid, cudaStream_t st);
+cudaError_t launch_update_a(const JobDesc &J, cudaStream_t st);
+cudaError_t launch_update_b(const JobDesc &J, cudaStream_t st);
+// batched rounds over the jobs of a device job table
+struct BatchMaps {
+    CUtensorMap m[4];  // the table arena as [lines][64 entries]; boxes of 32, 16, 8 and 4 lines
+};
+cudaError_t launch_bbegin(JobDesc *jobs, BatchMeta *meta, cudaStream_t st);
+cudaError_t launch_bscreen(const BatchMaps &maps, const JobDesc *jobs, const WorkItem *items,
+                           BatchMeta *meta, int max_words, const SearchShape &shape, bool interleaved,
+                           int grid, cudaStream_t st);
+cudaError_t launch_bshortlist(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st);
+cudaError_t launch_brescan(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st);
+cudaError_t launch_bupdate_a(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st);
+cudaError_t launch_bupdate_b(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st);
+size_t bscreen_smem_bytes(const SearchShape &s, int max_words);
+cudaError_t set_bscreen_smem_limit(int bytes);
 int update_grid(int n);
 
 }  // namespace vjb

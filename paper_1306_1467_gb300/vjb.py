@@ -19,8 +19,9 @@ import numpy as np
 from . import build as _build
 
 OK, DONE_PERFECT, DONE_NOGAIN = 0, 1, 2
-EINVAL, ESTATE, ENOMEM, ECUDA, EDEVICE = -1, -2, -3, -4, -5
+EINVAL, ESTATE, ENOMEM, ECUDA, EDEVICE, EFULL = -1, -2, -3, -4, -5, -6
 MAX_SAMPLES = 32766
+BATCH_INTERLEAVED = -1
 HAAR_TYPES = ("3H", "3V", "2H", "2V", "4")
 
 
@@ -83,6 +84,24 @@ class Timing(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
 
 
+class BatchInfo(C.Structure):
+    _fields_ = [("jobs", C.c_int32), ("warps", C.c_int32), ("stages", C.c_int32), ("unroll", C.c_int32),
+                ("rows_per_warp", C.c_int32), ("pad", C.c_int32), ("budget_bytes", C.c_int64),
+                ("free_bytes", C.c_int64), ("largest_free_bytes", C.c_int64),
+                ("search_bytes", C.c_double), ("launches", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class BatchTrial(C.Structure):
+    _fields_ = [("warps", C.c_int32), ("stages", C.c_int32), ("unroll", C.c_int32),
+                ("rows_per_warp", C.c_int32), ("ms_per_round", C.c_float)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 # Every exported symbol with its (restype, argtypes).
 _P, _I32, _I64 = C.c_void_p, C.c_int32, C.c_int64
 SIGNATURES = {
@@ -108,6 +127,20 @@ SIGNATURES = {
     "vjb_get_round_diag": (C.c_int, [_P, _I32, _I32, _P]),
     "vjb_set_timing": (C.c_int, [_P, _I32]),
     "vjb_get_timing": (C.c_int, [_P, _P]),
+    "vjb_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _P, _I64]),
+    "vjb_batch_destroy": (None, [_P]),
+    "vjb_batch_table_bytes": (C.c_int, [_I32, _I32, _I32, C.POINTER(C.c_int64)]),
+    "vjb_batch_add_job": (C.c_int, [_P, _P, _P, _I32, _I32, _I32, _I32, C.POINTER(C.c_int32)]),
+    "vjb_batch_remove_job": (C.c_int, [_P, _I32]),
+    "vjb_batch_train": (C.c_int, [_P, _I32, C.POINTER(C.c_int32)]),
+    "vjb_batch_autotune": (C.c_int, [_P, _I32, C.POINTER(C.c_int32), _P, _I32, C.POINTER(C.c_int32)]),
+    "vjb_batch_job_state": (C.c_int, [_P, _I32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "vjb_batch_get_stumps": (C.c_int, [_P, _I32, _I32, _I32, _P]),
+    "vjb_batch_get_weights": (C.c_int, [_P, _I32, _P]),
+    "vjb_batch_set_search_shape": (C.c_int, [_P, _P, _I32]),
+    "vjb_batch_get_info": (C.c_int, [_P, _P]),
+    "vjb_batch_set_timing": (C.c_int, [_P, _I32]),
+    "vjb_batch_get_timing": (C.c_int, [_P, _P]),
     "vjb_screen_noalloc": (C.c_int, [_P, _P, _I32, _I32, _I64, C.c_double, C.c_double, _I32,
                                      _P, _P, _P, _P]),
 }
@@ -312,3 +345,122 @@ class Trainer:
         out = np.zeros(nf, np.float32)
         self._check(self._lib.vjb_screen_errors(self._h, _ptr(out)))
         return out
+
+
+class Batch:
+    """Many training jobs trained together (``vjb_batch``): one launch of each
+    round kernel covers every job, and each job's stumps and weights are the
+    ones it would get alone in a :class:`Trainer`.
+
+    ``table_budget_bytes`` is the HBM arena for the jobs' sorted tables; a job
+    whose table does not fit what is free raises :class:`VJBError` with code
+    ``EFULL``.
+    """
+
+    def __init__(self, table_budget_bytes: int, device: int = 0, stream=None):
+        self._lib = load_library()
+        h = C.c_void_p()
+        s = None if stream is None else C.c_void_p(int(stream))
+        self._check(self._lib.vjb_batch_create(C.byref(h), int(device), s, int(table_budget_bytes)))
+        self._h = h
+        self.jobs = {}  # id -> n
+
+    def _check(self, rc: int) -> int:
+        if rc < 0:
+            raise VJBError(rc, self._lib.vjb_last_error().decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.vjb_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def table_bytes(n: int, h: int, w: int) -> int:
+        lib = load_library()
+        out = C.c_int64()
+        rc = lib.vjb_batch_table_bytes(int(n), int(h), int(w), C.byref(out))
+        if rc < 0:
+            raise VJBError(rc, lib.vjb_last_error().decode())
+        return int(out.value)
+
+    def add_job(self, pixels, labels, rounds: int) -> int:
+        """Add a job (host pixels [N, H, W] uint8, labels [N]); returns its id."""
+        px = np.ascontiguousarray(pixels, np.uint8)
+        y = np.ascontiguousarray(labels, np.uint8)
+        n, h, w = px.shape
+        if y.shape != (n,):
+            raise ValueError("labels must have shape [N]")
+        jid = C.c_int32()
+        self._check(self._lib.vjb_batch_add_job(self._h, _ptr(px), _ptr(y), n, h, w, int(rounds),
+                                                C.byref(jid)))
+        self.jobs[int(jid.value)] = int(n)
+        return int(jid.value)
+
+    def remove_job(self, job_id: int):
+        self._check(self._lib.vjb_batch_remove_job(self._h, int(job_id)))
+        self.jobs.pop(int(job_id), None)
+
+    def train(self, max_rounds: int = 1 << 30) -> int:
+        """Run batched rounds until every job is done or ``max_rounds`` ran; returns rounds run."""
+        r = C.c_int32()
+        self._check(self._lib.vjb_batch_train(self._h, int(max_rounds), C.byref(r)))
+        return int(r.value)
+
+    def autotune(self, trial_rounds: int = 2) -> int:
+        """Time real rounds with each candidate launch shape and keep the fastest; returns rounds
+        run.  The timed shapes are left in ``self.trials``."""
+        r, nt = C.c_int32(), C.c_int32()
+        arr = (BatchTrial * 32)()
+        self._check(self._lib.vjb_batch_autotune(self._h, int(trial_rounds), C.byref(r), arr, 32, C.byref(nt)))
+        self.trials = [arr[k].as_dict() for k in range(nt.value)]
+        return int(r.value)
+
+    def job_state(self, job_id: int):
+        """(kept stumps, status) of a job."""
+        d, st = C.c_int32(), C.c_int32()
+        self._check(self._lib.vjb_batch_job_state(self._h, int(job_id), C.byref(d), C.byref(st)))
+        return int(d.value), int(st.value)
+
+    def stumps(self, job_id: int) -> list:
+        done, _ = self.job_state(job_id)
+        arr = (Stump * max(done, 1))()
+        self._check(self._lib.vjb_batch_get_stumps(self._h, int(job_id), 0, done, arr))
+        return [arr[t].as_dict() for t in range(done)]
+
+    def get_weights(self, job_id: int) -> np.ndarray:
+        out = np.zeros(self.jobs[int(job_id)], np.float32)
+        self._check(self._lib.vjb_batch_get_weights(self._h, int(job_id), _ptr(out)))
+        return out
+
+    def set_search_shape(self, warps: int = 0, stages: int = 0, unroll: int = 0, rows_per_warp: int = 0):
+        """Batched search launch shape; rows_per_warp > 0 selects the work queue with that many
+        features per warp and item, BATCH_INTERLEAVED the interleaved schedule, 0 keeps it."""
+        sh = SearchShapeC(int(warps), int(stages), 0, int(unroll), 0)
+        self._check(self._lib.vjb_batch_set_search_shape(self._h, C.byref(sh), int(rows_per_warp)))
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        self._check(self._lib.vjb_batch_get_info(self._h, C.byref(i)))
+        return i.as_dict()
+
+    def set_timing(self, enable: bool = True):
+        """Enable (and reset) CUDA-event timing of every batched round and its search kernel."""
+        self._check(self._lib.vjb_batch_set_timing(self._h, 1 if enable else 0))
+
+    def timing(self) -> dict:
+        t = Timing()
+        self._check(self._lib.vjb_batch_get_timing(self._h, C.byref(t)))
+        return t.as_dict()
