@@ -56,6 +56,13 @@ def _args():
     p.add_argument("--batch-rounds", type=int, default=100)
     p.add_argument("--batch-n", type=int, nargs=2, default=(2000, 20000), metavar=("LO", "HI"),
                    help="batching form: range of the jobs' sample counts")
+    p.add_argument("--serve", action="store_true",
+                   help="serving form only: Poisson stream of training requests, continuous batching")
+    p.add_argument("--serve-rate", type=float, default=4.0, help="serving form: mean arrivals per second")
+    p.add_argument("--serve-seconds", type=float, default=30.0, help="serving form: arrival window")
+    p.add_argument("--serve-budget-gb", type=float, default=48.0, help="serving form: HBM for sorted tables")
+    p.add_argument("--serve-pool", type=int, default=16, help="serving form: distinct jobs the requests cycle over")
+    p.add_argument("--serve-rounds", type=int, default=50)
     return p.parse_args()
 
 
@@ -502,6 +509,92 @@ def batch_comparison(a, device: int = 0) -> dict:
             "identical_jobs": f"{equal}/{len(data)}"}
 
 
+def serve_report(a, device: int = 0) -> dict:
+    """Serving form: training requests arrive as a Poisson stream (`--serve-rate`
+    per second for `--serve-seconds`); each is a job of N uniform in
+    2,000..20,000 windows (positive fraction 0.2..0.5) at 24x24, or 20x20 for
+    1 in 4 and 32x32 for 1 in 8 of them, trained to `--serve-rounds` rounds.
+    The library's server admits requests against a fixed HBM budget for the
+    sorted tables and trains the admitted ones together (continuous
+    batching).  Requests cycle over a pool of distinct jobs whose results alone
+    (plain path) are computed first; every served result is compared with its
+    job's result alone."""
+    import numpy as np
+
+    from paper_1306_1467_gb300 import synth, vjb
+
+    rng = np.random.Generator(np.random.PCG64(1310))
+    pool = []
+    for k in range(a.serve_pool):
+        u = rng.uniform()
+        hw = 32 if u < 0.125 else (20 if u < 0.375 else 24)
+        n = int(rng.integers(2000, 20001))
+        n_pos = max(1, min(n - 1, int(round(rng.uniform(0.2, 0.5) * n))))
+        pool.append(synth.make_windows(n_pos, n - n_pos, hw, hw, seed=1310 * 1000 + k))
+    R = a.serve_rounds
+    alone = []
+    with vjb.Trainer(device) as tr:
+        for px, y in pool:
+            tr.prepare(px, y)
+            st, stumps = tr.train_strong(R)
+            alone.append((st, stumps, tr.get_weights()))
+    # arrival times
+    t, arrivals = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / a.serve_rate)
+        if t > a.serve_seconds:
+            break
+        arrivals.append(t)
+    budget = int(a.serve_budget_gb * 1e9)
+    ids = []
+    with vjb.Server(budget, max_jobs=64, device=device) as srv:
+        t0 = time.perf_counter()
+        k = 0
+        while True:
+            now = time.perf_counter() - t0
+            while k < len(arrivals) and arrivals[k] <= now:
+                px, y = pool[k % len(pool)]
+                ids.append((srv.submit(px, y, R), k % len(pool)))
+                k += 1
+            st = srv.stats()
+            busy = st["queued"] + st["preparing"] + st["training"]
+            if k == len(arrivals) and busy == 0:
+                break
+            if busy == 0:
+                time.sleep(max(0.0, min(arrivals[k] - (time.perf_counter() - t0), 0.05)))
+                continue
+            srv.step(1)
+        wall_s = time.perf_counter() - t0
+        infos = [srv.request(rid) for rid, _ in ids]
+        same = 0
+        for (rid, j), info in zip(ids, infos):
+            st, stumps, w = srv.result(rid)
+            st_a, stumps_a, w_a = alone[j]
+            same += int(st == st_a and stumps == stumps_a and np.array_equal(w, w_a))
+        ms, jobs = srv.round_times()
+        summary = srv.stats()
+    lat = np.array([i["t_done_ms"] - i["t_submit_ms"] for i in infos])
+    wait = np.array([i["t_admit_ms"] - i["t_submit_ms"] for i in infos])
+    prep = np.array([i["t_ready_ms"] - i["t_admit_ms"] for i in infos])
+    per_job_round = np.array([i["round_ms_sum"] / max(i["rounds_timed"], 1) for i in infos])
+    job_round_ms = np.repeat(ms, jobs)  # the latency each job saw for each of its rounds
+    q = lambda x: {"p50": float(np.percentile(x, 50)), "p99": float(np.percentile(x, 99)),  # noqa: E731
+                   "mean": float(np.mean(x)), "max": float(np.max(x))}
+    span_s = (max(i["t_done_ms"] for i in infos) - min(i["t_submit_ms"] for i in infos)) / 1000.0
+    return {"workload": (f"Poisson arrivals, mean {a.serve_rate}/s over {a.serve_seconds} s ({len(ids)} requests); "
+                         f"jobs of N uniform 2,000-20,000, positive fraction 0.2-0.5, 24x24 (20x20 for 1 in 4, "
+                         f"32x32 for 1 in 8), {R} rounds; requests cycle over {len(pool)} distinct jobs, seed 1310"),
+            "table_budget_bytes": budget, "max_jobs": 64,
+            "requests": len(ids), "identical_to_alone": f"{same}/{len(ids)}",
+            "job_rounds": int(summary["job_rounds"]), "batched_rounds": int(summary["rounds"]),
+            "job_rounds_per_s": summary["job_rounds"] / span_s, "span_s": span_s, "wall_s": wall_s,
+            "gpu_round_busy_frac": float(ms.sum()) / 1000.0 / span_s,
+            "latency_ms": {"per_job": q(lat), "admission_wait": q(wait), "preparation": q(prep),
+                           "per_round": q(job_round_ms), "batched_round": q(ms),
+                           "per_job_mean_round": q(per_job_round)},
+            "jobs_per_round": {"mean": float(jobs.mean()), "max": int(jobs.max())}}
+
+
 def main():
     a = _args()
     ws, rank, local = _dist()
@@ -510,6 +603,10 @@ def main():
         return
     if a.batch:
         print(json.dumps({"metric": "batching form: batched vs plain on one GPU", **batch_comparison(a, local)}),
+              flush=True)
+        return
+    if a.serve:
+        print(json.dumps({"metric": "serving form: continuous batching of training requests", **serve_report(a, local)}),
               flush=True)
         return
     if a.impl == "reference":

@@ -346,6 +346,83 @@ int vjb_batch_get_info(vjb_batch *b, vjb_batch_info *out);
 int vjb_batch_set_timing(vjb_batch *b, int32_t enable);
 int vjb_batch_get_timing(vjb_batch *b, vjb_timing *out);
 
+/* ---- serving: continuous batching of training requests ------------------------------
+ * A server trains requests as they arrive, many at a time, in one batch on
+ * one GPU.  A request (windows, labels, round count) waits in arrival order
+ * until its sorted table fits the free part of the table budget and a job
+ * slot is free; later requests may overtake one that does not fit, at most 8
+ * times.  An admitted request is prepared (integral images, features, sorted
+ * table) by a worker thread on its own stream while the batch keeps training
+ * the others, joins the batch at the next round and leaves it when it has
+ * kept `rounds` stumps (or stops early); its table space then goes to the
+ * requests still waiting.  Each request's stumps and weights are those of a
+ * plain run of the same job (see the batch section).
+ * Times are host milliseconds since the server was created; round times
+ * are CUDA-event durations of whole batched rounds. */
+typedef struct vjb_server vjb_server;
+
+#define VJB_REQ_QUEUED    0
+#define VJB_REQ_PREPARING 1
+#define VJB_REQ_TRAINING  2
+#define VJB_REQ_DONE      3
+#define VJB_REQ_FAILED    4
+
+typedef struct {
+    int64_t request_id;
+    int32_t state;            /* VJB_REQ_*                                            */
+    int32_t status;           /* VJB_OK, VJB_DONE_* or a negative code (failed)       */
+    int32_t rounds_done;      /* stumps kept so far                                  */
+    int32_t rounds_target;
+    int32_t n, h, w;
+    int32_t rounds_timed;     /* batched rounds it took part in                       */
+    int32_t pad;
+    int64_t table_bytes;      /* its share of the table budget                        */
+    double  t_submit_ms, t_admit_ms, t_ready_ms, t_done_ms;  /* -1 until reached      */
+    double  round_ms_sum;     /* summed duration of the rounds it took part in        */
+} vjb_request_info;
+
+typedef struct {
+    int32_t queued, preparing, training, done, failed, pad;
+    int64_t rounds;           /* batched rounds run                                   */
+    int64_t job_rounds;       /* rounds summed over the jobs in them                  */
+    int64_t budget_bytes, free_bytes;
+    double  round_ms_total;   /* device time of all batched rounds                    */
+    double  clock_ms;         /* time since creation                                  */
+} vjb_server_summary;
+
+/* Create a server on `device` with `table_budget_bytes` of HBM for sorted
+ * tables and at most `max_jobs` (1-256) requests admitted at once. */
+int vjb_server_create(vjb_server **out, int device, int64_t table_budget_bytes, int32_t max_jobs);
+/* Stops the worker (requests still queued are dropped) and frees everything. */
+void vjb_server_destroy(vjb_server *s);
+
+/* Queue a request (host windows [n][h][w] and labels [n], copied).  Errors:
+ * VJB_EINVAL (sizes, labels), VJB_EFULL (its table exceeds the whole budget). */
+int vjb_server_submit(vjb_server *s, const uint8_t *pixels, const uint8_t *labels, int32_t n, int32_t h,
+                      int32_t w, int32_t rounds, int64_t *request_id);
+
+/* One scheduling step: admit what fits, take in prepared requests, then run
+ * up to `max_rounds` batched rounds, retiring finished jobs and admitting
+ * waiting requests between rounds.  When nothing trains but a request is
+ * being prepared it waits for it up to 5 ms.  *rounds_run (may be NULL)
+ * receives the rounds run. */
+int vjb_server_step(vjb_server *s, int32_t max_rounds, int32_t *rounds_run);
+
+/* State and times of a request. */
+int vjb_server_request(vjb_server *s, int64_t request_id, vjb_request_info *out);
+
+/* A finished request's stumps (`cap` of room; may be NULL) and final
+ * weights ([n], may be NULL).  Returns its status; VJB_ESTATE while it runs. */
+int vjb_server_result(vjb_server *s, int64_t request_id, vjb_stump *stumps, int32_t cap, float *weights);
+
+/* Forget a finished request. */
+int vjb_server_release(vjb_server *s, int64_t request_id);
+
+int vjb_server_stats(vjb_server *s, vjb_server_summary *out);
+
+/* Duration and job count of batched rounds [first, first + count). */
+int vjb_server_round_times(vjb_server *s, int64_t first, int32_t count, float *ms, int32_t *jobs);
+
 /* ---- allocation-free search ----------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that cannot allocate device memory when they want a search -- a host that

@@ -9,8 +9,15 @@
 
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "vjb_internal.cuh"
@@ -1193,19 +1200,22 @@ bool batch_shape_ok(const vjb_batch *b, const SearchShape &s) {
 
 // Largest number of rounds a job of the batch still wants (0 when all are
 // done); grows the jobs' stump records to their targets.
-int batch_rounds_wanted(vjb_batch *b, int *want) {
+int batch_rounds_wanted(vjb_batch *b, int *want, std::vector<RoundState> *states = nullptr) {
     *want = 0;
-    for (auto &s : b->slots) {
-        RoundState rs;
-        CK(cudaMemcpyAsync(&rs, s.ctx->d_rs, sizeof rs, cudaMemcpyDeviceToHost, b->stream));
-        CK(cudaStreamSynchronize(b->stream));
-        if (rs.status == VJB_OK && !rs.flags) *want = std::max(*want, s.round_target - rs.rounds);
+    std::vector<RoundState> st(b->slots.size());
+    for (size_t k = 0; k < st.size(); ++k)
+        CK(cudaMemcpyAsync(&st[k], b->slots[k].ctx->d_rs, sizeof(RoundState), cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaStreamSynchronize(b->stream));
+    for (size_t k = 0; k < st.size(); ++k) {
+        BatchSlot &s = b->slots[k];
+        if (st[k].status == VJB_OK && !st[k].flags) *want = std::max(*want, s.round_target - st[k].rounds);
         if (s.round_target > s.ctx->stump_cap) {
             const int rc = ensure_stump_cap(s.ctx, s.round_target);
             if (rc) return rc;
             b->dirty = true;
         }
     }
+    if (states) states->swap(st);
     return VJB_OK;
 }
 
@@ -1551,6 +1561,436 @@ int vjb_batch_get_info(vjb_batch *b, vjb_batch_info *out) {
     for (const auto &s : b->slots) bytes += 2.0 * (double)s.ctx->nfeat * s.ctx->n;
     out->search_bytes = bytes;
     out->launches = b->launches;
+    return VJB_OK;
+}
+
+}  // extern "C"
+
+// ---- serving: continuous batching of training requests ---------------------------------
+// A server keeps one batch on the device.  Requests wait in arrival order
+// until their sorted table fits the free part of the batch's arena (and a job
+// slot is free); a worker thread then prepares each admitted request on its
+// own stream -- windows, integral images, features, sorted table written into
+// the arena -- while the main thread keeps running batched rounds for the jobs
+// already training.  A prepared request joins the batch at the next round;
+// a job that reaches its round count (or stops early) leaves it, its stumps
+// and weights are copied to the host and its table space is freed for the
+// requests still waiting.
+
+namespace {
+
+enum { kReqQueued = 0, kReqPreparing = 1, kReqTraining = 2, kReqDone = 3, kReqFailed = 4 };
+constexpr int kMaxBypass = 8;  // later requests may overtake a waiting one this often
+
+struct ServerReq {
+    int64_t id = 0;
+    std::vector<uint8_t> px, y;
+    int32_t n = 0, h = 0, w = 0, rounds = 0;
+    int state = kReqQueued;
+    int status = VJB_OK;
+    int64_t line_first = 0, line_count = 0;
+    vjb_ctx *ctx = nullptr;
+    int32_t slot = -1;
+    double t_submit = 0, t_admit = -1, t_ready = -1, t_done = -1;
+    double round_ms_sum = 0;
+    int32_t rounds_timed = 0;
+    int bypassed = 0;
+    std::vector<vjb_stump> stumps;
+    std::vector<float> weights;
+    std::string error;
+};
+
+}  // namespace
+
+struct vjb_server {
+    vjb_batch *b = nullptr;
+    int device = 0;
+    int max_jobs = 0;
+    std::chrono::steady_clock::time_point t0;
+    std::map<int64_t, std::unique_ptr<ServerReq>> reqs;
+    std::deque<ServerReq *> queue;  // waiting for admission, in arrival order
+    int64_t next_id = 1;
+    // worker thread and what it shares with the main thread (under mu)
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<ServerReq *> to_prepare;
+    std::vector<ServerReq *> prepared;
+    bool stop = false;
+    int preparing = 0;  // admitted, not yet collected (main thread only)
+    std::vector<float> round_ms;
+    std::vector<int32_t> round_jobs;
+    int64_t job_rounds = 0;
+
+    double now_ms() const {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+// Worker side: build a request's context with its table in the arena.
+int server_prepare(vjb_server *s, ServerReq *r) {
+    vjb_ctx *c = nullptr;
+    int rc = vjb_create(&c, s->device, nullptr);
+    if (rc == VJB_OK) rc = vjb_load_windows(c, r->px.data(), r->y.data(), r->n, r->h, r->w);
+    if (rc == VJB_OK) {
+        c->rows_external = true;
+        c->d_rows = s->b->arena + r->line_first * kLineElems;
+        c->line_base = r->line_first;
+        rc = vjb_build_integral(c);
+    }
+    int64_t cnt = 0;
+    if (rc == VJB_OK) rc = vjb_enumerate_haar(c, &cnt, nullptr);
+    if (rc == VJB_OK) rc = ensure_stump_cap(c, std::max(r->rounds, 1));
+    if (rc != VJB_OK) {
+        r->error = vjb_last_error();
+        if (c) vjb_destroy(c);
+        return rc;
+    }
+    r->ctx = c;
+    return VJB_OK;
+}
+
+void server_worker(vjb_server *s) {
+    cudaSetDevice(s->device);
+    for (;;) {
+        ServerReq *r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait(lk, [&] { return s->stop || !s->to_prepare.empty(); });
+            if (s->to_prepare.empty()) return;  // stop requested and nothing left
+            r = s->to_prepare.front();
+            s->to_prepare.pop_front();
+        }
+        const int rc = s->stop ? VJB_ESTATE : server_prepare(s, r);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            if (rc != VJB_OK) {
+                r->status = rc;
+                if (r->error.empty()) r->error = "server stopped before the request was prepared";
+            }
+            s->prepared.push_back(r);
+        }
+        s->cv_done.notify_all();
+    }
+}
+
+// Main side: move prepared requests into the batch (or to failed).
+void server_collect(vjb_server *s, bool wait) {
+    std::vector<ServerReq *> got;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (wait && s->prepared.empty() && s->preparing > 0)
+            s->cv_done.wait_for(lk, std::chrono::milliseconds(5), [&] { return !s->prepared.empty(); });
+        got.swap(s->prepared);
+    }
+    for (ServerReq *r : got) {
+        s->preparing -= 1;
+        r->t_ready = s->now_ms();
+        if (r->status != VJB_OK) {
+            arena_give(s->b, r->line_first, r->line_count);
+            r->state = kReqFailed;
+            r->t_done = r->t_ready;
+            continue;
+        }
+        BatchSlot sl;
+        sl.ctx = r->ctx;
+        sl.id = s->b->next_id++;
+        sl.line_base = r->line_first;
+        sl.line_count = r->line_count;
+        sl.round_target = r->rounds;
+        s->b->slots.push_back(sl);
+        s->b->dirty = true;
+        r->slot = sl.id;
+        r->state = kReqTraining;
+    }
+}
+
+ServerReq *req_of_slot(vjb_server *s, int32_t slot) {
+    for (auto &kv : s->reqs)
+        if (kv.second->state == kReqTraining && kv.second->slot == slot) return kv.second.get();
+    return nullptr;
+}
+
+// Jobs that reached their round count or stopped leave the batch.
+int server_retire(vjb_server *s, const std::vector<RoundState> &st) {
+    vjb_batch *b = s->b;
+    std::vector<BatchSlot> keep;
+    for (size_t k = 0; k < b->slots.size(); ++k) {
+        const BatchSlot &sl = b->slots[k];
+        const RoundState &rs = st[k];
+        const bool done = rs.flags || rs.status != VJB_OK || rs.rounds >= sl.round_target;
+        if (!done) {
+            keep.push_back(sl);
+            continue;
+        }
+        ServerReq *r = req_of_slot(s, sl.id);
+        if (r) {
+            r->status = rs.flags ? VJB_EDEVICE : rs.status;
+            r->stumps.resize((size_t)rs.rounds);
+            if (rs.rounds) CK(cudaMemcpy(r->stumps.data(), sl.ctx->d_stumps, sizeof(vjb_stump) * rs.rounds, cudaMemcpyDeviceToHost));
+            r->weights.resize((size_t)r->n);
+            CK(cudaMemcpy(r->weights.data(), sl.ctx->d_w, sizeof(float) * r->n, cudaMemcpyDeviceToHost));
+            r->state = kReqDone;
+            r->t_done = s->now_ms();
+            r->ctx = nullptr;
+            r->px.clear();
+            r->px.shrink_to_fit();
+        }
+        vjb_destroy(sl.ctx);
+        arena_give(b, sl.line_base, sl.line_count);
+        b->dirty = true;
+    }
+    b->slots.swap(keep);
+    return VJB_OK;
+}
+
+// Waiting requests whose tables fit the free arena are handed to the worker,
+// in arrival order; later ones may overtake one that does not fit, at most
+// kMaxBypass times, so that a large table is not starved.
+void server_admit(vjb_server *s) {
+    int active = (int)s->b->slots.size() + s->preparing;
+    bool blocked = false;
+    for (auto it = s->queue.begin(); it != s->queue.end() && active < s->max_jobs;) {
+        ServerReq *r = *it;
+        int64_t first = 0;
+        if (arena_take(s->b, r->line_count, &first)) {
+            r->line_first = first;
+            r->state = kReqPreparing;
+            r->t_admit = s->now_ms();
+            {
+                std::lock_guard<std::mutex> lk(s->mu);
+                s->to_prepare.push_back(r);
+            }
+            s->cv_work.notify_one();
+            s->preparing += 1;
+            active += 1;
+            it = s->queue.erase(it);
+            // the requests this one overtook
+            for (auto jt = s->queue.begin(); jt != it; ++jt) (*jt)->bypassed += 1;
+        } else {
+            if (r->bypassed >= kMaxBypass) blocked = true;
+            if (blocked) break;
+            ++it;
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int vjb_server_create(vjb_server **out, int device, int64_t table_budget_bytes, int32_t max_jobs) {
+    g_err[0] = 0;
+    if (!out) return fail(VJB_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (max_jobs < 1 || max_jobs > kMaxBatchJobs)
+        return fail(VJB_EINVAL, "max_jobs = %d outside [1, %d]", max_jobs, kMaxBatchJobs);
+    vjb_batch *b = nullptr;
+    int rc = vjb_batch_create(&b, device, nullptr, table_budget_bytes);
+    if (rc) return rc;
+    vjb_server *s = new vjb_server();
+    s->b = b;
+    s->device = device;
+    s->max_jobs = max_jobs;
+    s->t0 = std::chrono::steady_clock::now();
+    s->worker = std::thread(server_worker, s);
+    *out = s;
+    return VJB_OK;
+}
+
+void vjb_server_destroy(vjb_server *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+    }
+    s->cv_work.notify_all();
+    if (s->worker.joinable()) s->worker.join();
+    cudaSetDevice(s->device);
+    for (ServerReq *r : s->prepared)
+        if (r->ctx) vjb_destroy(r->ctx);
+    vjb_batch_destroy(s->b);  // destroys the contexts of the training jobs
+    delete s;
+}
+
+int vjb_server_submit(vjb_server *s, const uint8_t *pixels, const uint8_t *labels, int32_t n, int32_t h,
+                      int32_t w, int32_t rounds, int64_t *request_id) {
+    g_err[0] = 0;
+    if (!s || !pixels || !labels || !request_id) return fail(VJB_EINVAL, "NULL argument");
+    if (rounds < 1) return fail(VJB_EINVAL, "rounds = %d < 1", rounds);
+    if (n < 2 || n > VJB_MAX_SAMPLES || h < 1 || w < 1 || h > VJB_MAX_WINDOW || w > VJB_MAX_WINDOW)
+        return fail(VJB_EINVAL, "sizes outside the limits");
+    int rc = validate_labels(labels, n);
+    if (rc) return rc;
+    const int64_t need = table_lines(n, h, w);
+    if (need == 0) return fail(VJB_EINVAL, "window %dx%d has no feature", w, h);
+    if (need > s->b->arena_lines)
+        return fail(VJB_EFULL, "table of %lld bytes exceeds the whole budget of %lld", (long long)(need * kLineBytes),
+                    (long long)(s->b->arena_lines * kLineBytes));
+    auto r = std::make_unique<ServerReq>();
+    r->id = s->next_id++;
+    r->px.assign(pixels, pixels + (size_t)n * h * w);
+    r->y.assign(labels, labels + n);
+    r->n = n;
+    r->h = h;
+    r->w = w;
+    r->rounds = rounds;
+    r->line_count = need;
+    r->t_submit = s->now_ms();
+    s->queue.push_back(r.get());
+    *request_id = r->id;
+    s->reqs[r->id] = std::move(r);
+    return VJB_OK;
+}
+
+int vjb_server_step(vjb_server *s, int32_t max_rounds, int32_t *rounds_run) {
+    g_err[0] = 0;
+    if (!s || max_rounds < 0) return fail(VJB_EINVAL, "bad argument");
+    if (rounds_run) *rounds_run = 0;
+    CK(cudaSetDevice(s->device));
+    vjb_batch *b = s->b;
+    server_admit(s);
+    server_collect(s, b->slots.empty());
+    int ran = 0;
+    for (; ran < max_rounds; ++ran) {
+        int want = 0;
+        std::vector<RoundState> st;
+        int rc = batch_rounds_wanted(b, &want, &st);
+        if (rc) return rc;
+        rc = server_retire(s, st);
+        if (rc) return rc;
+        if (want == 0) break;
+        int in_round = 0;
+        for (size_t k = 0; k < st.size(); ++k)
+            if (st[k].status == VJB_OK && !st[k].flags && st[k].rounds < b->slots[k].round_target) ++in_round;
+        std::vector<ServerReq *> members;
+        for (auto &sl : b->slots) {
+            ServerReq *r = req_of_slot(s, sl.id);
+            if (r) members.push_back(r);
+        }
+        float ms = 0.f;
+        rc = batch_run(b, 1, &ms);
+        if (rc) return rc;
+        s->round_ms.push_back(ms);
+        s->round_jobs.push_back(in_round);
+        s->job_rounds += in_round;
+        for (ServerReq *r : members) {
+            r->round_ms_sum += ms;
+            r->rounds_timed += 1;
+        }
+        server_admit(s);
+        server_collect(s, false);
+    }
+    // retire what the last round finished
+    {
+        int want = 0;
+        std::vector<RoundState> st;
+        int rc = batch_rounds_wanted(b, &want, &st);
+        if (rc) return rc;
+        rc = server_retire(s, st);
+        if (rc) return rc;
+        server_admit(s);
+    }
+    if (rounds_run) *rounds_run = ran;
+    return VJB_OK;
+}
+
+int vjb_server_request(vjb_server *s, int64_t request_id, vjb_request_info *out) {
+    g_err[0] = 0;
+    if (!s || !out) return fail(VJB_EINVAL, "NULL argument");
+    auto it = s->reqs.find(request_id);
+    if (it == s->reqs.end()) return fail(VJB_EINVAL, "no request %lld", (long long)request_id);
+    const ServerReq &r = *it->second;
+    memset(out, 0, sizeof *out);
+    out->request_id = r.id;
+    out->state = r.state;
+    out->status = r.status;
+    out->rounds_done = (int32_t)r.stumps.size();
+    out->rounds_target = r.rounds;
+    out->n = r.n;
+    out->h = r.h;
+    out->w = r.w;
+    out->rounds_timed = r.rounds_timed;
+    out->table_bytes = r.line_count * kLineBytes;
+    out->t_submit_ms = r.t_submit;
+    out->t_admit_ms = r.t_admit;
+    out->t_ready_ms = r.t_ready;
+    out->t_done_ms = r.t_done;
+    out->round_ms_sum = r.round_ms_sum;
+    if (r.state == kReqTraining) {
+        RoundState rs;
+        CK(cudaMemcpy(&rs, r.ctx->d_rs, sizeof rs, cudaMemcpyDeviceToHost));
+        out->rounds_done = rs.rounds;
+    }
+    if (r.state == kReqFailed) fail(r.status, "%s", r.error.c_str());
+    return VJB_OK;
+}
+
+int vjb_server_result(vjb_server *s, int64_t request_id, vjb_stump *stumps, int32_t cap, float *weights) {
+    g_err[0] = 0;
+    if (!s) return fail(VJB_EINVAL, "server is NULL");
+    auto it = s->reqs.find(request_id);
+    if (it == s->reqs.end()) return fail(VJB_EINVAL, "no request %lld", (long long)request_id);
+    const ServerReq &r = *it->second;
+    if (r.state == kReqFailed) return fail(r.status, "%s", r.error.c_str());
+    if (r.state != kReqDone) return fail(VJB_ESTATE, "request %lld is not finished", (long long)request_id);
+    if (stumps) {
+        if (cap < (int32_t)r.stumps.size()) return fail(VJB_EINVAL, "cap %d < %zu stumps", cap, r.stumps.size());
+        if (!r.stumps.empty()) memcpy(stumps, r.stumps.data(), sizeof(vjb_stump) * r.stumps.size());
+    }
+    if (weights) memcpy(weights, r.weights.data(), sizeof(float) * r.weights.size());
+    return r.status;
+}
+
+int vjb_server_release(vjb_server *s, int64_t request_id) {
+    g_err[0] = 0;
+    if (!s) return fail(VJB_EINVAL, "server is NULL");
+    auto it = s->reqs.find(request_id);
+    if (it == s->reqs.end()) return fail(VJB_EINVAL, "no request %lld", (long long)request_id);
+    if (it->second->state != kReqDone && it->second->state != kReqFailed)
+        return fail(VJB_ESTATE, "request %lld is not finished", (long long)request_id);
+    s->reqs.erase(it);
+    return VJB_OK;
+}
+
+int vjb_server_stats(vjb_server *s, vjb_server_summary *out) {
+    g_err[0] = 0;
+    if (!s || !out) return fail(VJB_EINVAL, "NULL argument");
+    memset(out, 0, sizeof *out);
+    for (auto &kv : s->reqs) {
+        switch (kv.second->state) {
+        case kReqQueued: out->queued += 1; break;
+        case kReqPreparing: out->preparing += 1; break;
+        case kReqTraining: out->training += 1; break;
+        case kReqDone: out->done += 1; break;
+        default: out->failed += 1;
+        }
+    }
+    out->rounds = (int64_t)s->round_ms.size();
+    out->job_rounds = s->job_rounds;
+    int64_t free_lines = 0;
+    for (const auto &fr : s->b->free_list) free_lines += fr.second;
+    out->budget_bytes = s->b->arena_lines * kLineBytes;
+    out->free_bytes = free_lines * kLineBytes;
+    double busy = 0.0;
+    for (float m : s->round_ms) busy += m;
+    out->round_ms_total = busy;
+    out->clock_ms = s->now_ms();
+    return VJB_OK;
+}
+
+int vjb_server_round_times(vjb_server *s, int64_t first, int32_t count, float *ms, int32_t *jobs) {
+    g_err[0] = 0;
+    if (!s) return fail(VJB_EINVAL, "server is NULL");
+    if (first < 0 || count < 0 || first + count > (int64_t)s->round_ms.size())
+        return fail(VJB_EINVAL, "rounds [%lld, %lld) outside the %zu run", (long long)first,
+                    (long long)(first + count), s->round_ms.size());
+    for (int32_t k = 0; k < count; ++k) {
+        if (ms) ms[k] = s->round_ms[(size_t)(first + k)];
+        if (jobs) jobs[k] = s->round_jobs[(size_t)(first + k)];
+    }
     return VJB_OK;
 }
 

@@ -21,6 +21,7 @@ from . import build as _build
 OK, DONE_PERFECT, DONE_NOGAIN = 0, 1, 2
 EINVAL, ESTATE, ENOMEM, ECUDA, EDEVICE, EFULL = -1, -2, -3, -4, -5, -6
 MAX_SAMPLES = 32766
+REQ_QUEUED, REQ_PREPARING, REQ_TRAINING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3, 4
 BATCH_INTERLEAVED = -1
 HAAR_TYPES = ("3H", "3V", "2H", "2V", "4")
 
@@ -102,6 +103,27 @@ class BatchTrial(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class RequestInfo(C.Structure):
+    _fields_ = [("request_id", C.c_int64), ("state", C.c_int32), ("status", C.c_int32),
+                ("rounds_done", C.c_int32), ("rounds_target", C.c_int32), ("n", C.c_int32),
+                ("h", C.c_int32), ("w", C.c_int32), ("rounds_timed", C.c_int32), ("pad", C.c_int32),
+                ("table_bytes", C.c_int64), ("t_submit_ms", C.c_double), ("t_admit_ms", C.c_double),
+                ("t_ready_ms", C.c_double), ("t_done_ms", C.c_double), ("round_ms_sum", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class ServerSummary(C.Structure):
+    _fields_ = [("queued", C.c_int32), ("preparing", C.c_int32), ("training", C.c_int32),
+                ("done", C.c_int32), ("failed", C.c_int32), ("pad", C.c_int32), ("rounds", C.c_int64),
+                ("job_rounds", C.c_int64), ("budget_bytes", C.c_int64), ("free_bytes", C.c_int64),
+                ("round_ms_total", C.c_double), ("clock_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 # Every exported symbol with its (restype, argtypes).
 _P, _I32, _I64 = C.c_void_p, C.c_int32, C.c_int64
 SIGNATURES = {
@@ -141,6 +163,15 @@ SIGNATURES = {
     "vjb_batch_get_info": (C.c_int, [_P, _P]),
     "vjb_batch_set_timing": (C.c_int, [_P, _I32]),
     "vjb_batch_get_timing": (C.c_int, [_P, _P]),
+    "vjb_server_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, _I64, _I32]),
+    "vjb_server_destroy": (None, [_P]),
+    "vjb_server_submit": (C.c_int, [_P, _P, _P, _I32, _I32, _I32, _I32, C.POINTER(C.c_int64)]),
+    "vjb_server_step": (C.c_int, [_P, _I32, C.POINTER(C.c_int32)]),
+    "vjb_server_request": (C.c_int, [_P, _I64, _P]),
+    "vjb_server_result": (C.c_int, [_P, _I64, _P, _I32, _P]),
+    "vjb_server_release": (C.c_int, [_P, _I64]),
+    "vjb_server_stats": (C.c_int, [_P, _P]),
+    "vjb_server_round_times": (C.c_int, [_P, _I64, _I32, _P, _P]),
     "vjb_screen_noalloc": (C.c_int, [_P, _P, _I32, _I32, _I64, C.c_double, C.c_double, _I32,
                                      _P, _P, _P, _P]),
 }
@@ -464,3 +495,89 @@ class Batch:
         t = Timing()
         self._check(self._lib.vjb_batch_get_timing(self._h, C.byref(t)))
         return t.as_dict()
+
+
+class Server:
+    """Continuous batching of training requests on one GPU (``vjb_server``).
+
+    ``submit`` queues a request; ``step`` admits what fits the table budget,
+    lets the library's worker thread prepare admitted requests while the batch
+    trains, and runs batched rounds.  Every request's stumps and weights equal
+    those of a plain run of the same job.
+    """
+
+    def __init__(self, table_budget_bytes: int, max_jobs: int = 64, device: int = 0):
+        self._lib = load_library()
+        h = C.c_void_p()
+        self._check(self._lib.vjb_server_create(C.byref(h), int(device), int(table_budget_bytes), int(max_jobs)))
+        self._h = h
+        self._n = {}
+
+    def _check(self, rc: int) -> int:
+        if rc < 0:
+            raise VJBError(rc, self._lib.vjb_last_error().decode())
+        return rc
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.vjb_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, pixels, labels, rounds: int) -> int:
+        px = np.ascontiguousarray(pixels, np.uint8)
+        y = np.ascontiguousarray(labels, np.uint8)
+        n, h, w = px.shape
+        if y.shape != (n,):
+            raise ValueError("labels must have shape [N]")
+        rid = C.c_int64()
+        self._check(self._lib.vjb_server_submit(self._h, _ptr(px), _ptr(y), n, h, w, int(rounds), C.byref(rid)))
+        self._n[int(rid.value)] = (int(n), int(rounds))
+        return int(rid.value)
+
+    def step(self, max_rounds: int = 1) -> int:
+        r = C.c_int32()
+        self._check(self._lib.vjb_server_step(self._h, int(max_rounds), C.byref(r)))
+        return int(r.value)
+
+    def request(self, rid: int) -> dict:
+        i = RequestInfo()
+        self._check(self._lib.vjb_server_request(self._h, int(rid), C.byref(i)))
+        return i.as_dict()
+
+    def result(self, rid: int):
+        """(status, stumps, weights) of a finished request."""
+        n, rounds = self._n[int(rid)]
+        arr = (Stump * max(rounds, 1))()
+        w = np.zeros(n, np.float32)
+        st = self._check(self._lib.vjb_server_result(self._h, int(rid), arr, rounds, _ptr(w)))
+        done = self.request(rid)["rounds_done"]
+        return st, [arr[t].as_dict() for t in range(done)], w
+
+    def release(self, rid: int):
+        self._check(self._lib.vjb_server_release(self._h, int(rid)))
+        self._n.pop(int(rid), None)
+
+    def stats(self) -> dict:
+        s = ServerSummary()
+        self._check(self._lib.vjb_server_stats(self._h, C.byref(s)))
+        return s.as_dict()
+
+    def round_times(self):
+        """(durations in ms, jobs in the round) of every batched round so far."""
+        k = self.stats()["rounds"]
+        ms = np.zeros(max(k, 1), np.float32)
+        jobs = np.zeros(max(k, 1), np.int32)
+        self._check(self._lib.vjb_server_round_times(self._h, 0, int(k), _ptr(ms), _ptr(jobs)))
+        return ms[:k], jobs[:k]

@@ -154,7 +154,8 @@ def test_trajectory_against_independent_fp64_oracle(tiny_prepared):
 
 
 @pytest.mark.parametrize("n_pos,n_neg,h,w", [(300, 477, 9, 7), (5, 3, 4, 4), (1, 1, 3, 3),
-                                             (700, 1400, 12, 16), (1, 2, 1, 2)])
+                                             (700, 1400, 12, 16), (1, 2, 1, 2), (60, 140, 20, 20),
+                                             (50, 150, 32, 32)])
 def test_ragged_shapes(n_pos, n_neg, h, w):
     """Sample counts that leave ragged TMA boxes, units and lanes; odd windows."""
     from paper_1306_1467_gb300 import vjb

@@ -1,0 +1,96 @@
+"""Serving (vjb_server_*): continuous batching of training requests.
+
+Requests arrive while others train, wait for table space in a small budget,
+are prepared by the library's worker thread while the batch keeps training,
+join the batch between rounds and leave it when done.  Each request's result
+-- stumps and FP32 weights -- must be the one it gets alone (a plain run of
+the same job), bit for bit, whatever company it trained in.
+"""
+
+import numpy as np
+import pytest
+
+from paper_1306_1467_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(px, y, rounds):
+    from paper_1306_1467_gb300 import vjb
+    with vjb.Trainer(0) as tr:
+        tr.prepare(px, y)
+        st, stumps = tr.train_strong(rounds)
+        return st, stumps, tr.get_weights()
+
+
+def _requests():
+    # (n_pos, n_neg, h, w, seed, rounds): uneven sizes, three window sizes
+    spec = [(300, 700, 12, 12, 81, 6), (900, 1300, 10, 10, 82, 9), (200, 250, 14, 14, 83, 4),
+            (1200, 2000, 12, 12, 84, 7), (500, 600, 16, 16, 85, 5), (700, 900, 10, 10, 86, 8)]
+    return [(*synth.make_windows(p, q, h, w, seed=sd), r) for (p, q, h, w, sd, r) in spec]
+
+
+def test_serving_results_equal_alone_and_budget_is_respected():
+    from paper_1306_1467_gb300 import vjb
+    reqs = _requests()
+    tb = [vjb.Batch.table_bytes(px.shape[0], px.shape[1], px.shape[2]) for px, _, _ in reqs]
+    budget = sorted(tb)[-1] + sorted(tb)[-2]  # the two largest tables, not all of them
+    assert sum(tb) > budget
+    with vjb.Server(budget, max_jobs=3) as srv:
+        ids = [srv.submit(px, y, r) for px, y, r in reqs[:4]]
+        late = False
+        for it in range(100000):
+            st = srv.stats()
+            assert st["training"] + st["preparing"] <= 3
+            if not late and st["training"] >= 1 and st["rounds"] >= 2:
+                # later arrivals, while the first ones train
+                ids += [srv.submit(px, y, r) for px, y, r in reqs[4:]]
+                late = True
+            srv.step(1)
+            st = srv.stats()
+            if late and st["done"] + st["failed"] == len(reqs):
+                break
+        assert srv.stats()["done"] == len(reqs)
+        ms, jobs = srv.round_times()
+        assert len(ms) == srv.stats()["rounds"] and (ms > 0).all() and (jobs >= 1).all()
+        assert srv.stats()["job_rounds"] == int(jobs.sum())
+        assert (jobs >= 2).any()  # requests trained together
+        infos = [srv.request(rid) for rid in ids]
+        for info in infos:
+            assert info["state"] == vjb.REQ_DONE
+            assert info["t_submit_ms"] <= info["t_admit_ms"] <= info["t_ready_ms"] <= info["t_done_ms"]
+        # some request could only start once another had finished (budget or slots)
+        assert any(a["t_admit_ms"] >= b["t_done_ms"] for a in infos for b in infos)
+        # the late ones arrived while others were training
+        assert min(i["t_submit_ms"] for i in infos[4:]) > min(i["t_ready_ms"] for i in infos[:4])
+        for rid, (px, y, r) in zip(ids, reqs):
+            st, stumps, w = srv.result(rid)
+            st_a, stumps_a, w_a = _alone(px, y, r)
+            assert st == st_a and stumps == stumps_a, rid
+            assert np.array_equal(w, w_a), rid
+            srv.release(rid)
+        assert srv.stats()["free_bytes"] == srv.stats()["budget_bytes"]
+
+
+def test_serving_rejections():
+    from paper_1306_1467_gb300 import vjb
+    px, y = synth.make_windows(300, 300, 12, 12, seed=91)
+    with vjb.Server(vjb.Batch.table_bytes(600, 12, 12) - 128, max_jobs=2) as srv:
+        with pytest.raises(vjb.VJBError) as ei:
+            srv.submit(px, y, 3)  # its table can never fit
+        assert ei.value.code == vjb.EFULL
+        px2, y2 = synth.make_windows(100, 100, 8, 8, seed=92)
+        bad = y2.copy()
+        bad[0] = 2
+        with pytest.raises(vjb.VJBError) as ei:
+            srv.submit(px2, bad, 3)
+        assert ei.value.code == vjb.EINVAL
+        rid = srv.submit(px2, y2, 3)
+        with pytest.raises(vjb.VJBError) as ei:
+            srv.result(rid)  # not finished
+        assert ei.value.code == vjb.ESTATE
+        while srv.request(rid)["state"] != vjb.REQ_DONE:
+            srv.step(4)
+        st, stumps, _ = srv.result(rid)
+        st_a, stumps_a, _ = _alone(px2, y2, 3)
+        assert st == st_a and stumps == stumps_a
