@@ -82,11 +82,21 @@ def _peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def search_source_digest() -> str:
+    """SHA-256 of the plain search kernel's source: k_screen with the helpers
+    it uses in its file, and the device header."""
+    src = open(SEARCH_SRC).read()
+    a = src.index("// Predicated running max/min")
+    b = src.index("cudaError_t launch_screen(")
+    dev = open(os.path.join(os.path.dirname(SEARCH_SRC), "vjb_device.cuh")).read()
+    return hashlib.sha256((src[a:b] + dev).encode()).hexdigest()
+
+
 def _traffic():
     """DRAM bytes per search launch from the committed ncu summary, if it was
     taken on the current kernel source."""
     try:
-        sha = hashlib.sha256(open(SEARCH_SRC, "rb").read()).hexdigest()
+        sha = search_source_digest()
         kv = {}
         for line in open(PROFILE):
             if ":" in line and not line.startswith("#"):

@@ -258,6 +258,20 @@ int vjb_get_round_diag(vjb_ctx *ctx, int32_t first, int32_t count, vjb_round_dia
 int vjb_set_timing(vjb_ctx *ctx, int32_t enable);
 int vjb_get_timing(vjb_ctx *ctx, vjb_timing *out);
 
+/* ---- the strong classifier ------------------------------------------------------
+ * vjb_classify: the final hypothesis of Sec. 2.3 on n windows of the
+ * context's size (host pixels [n][h][w], copied):
+ *     score(x) = sum_t alpha_t h_t(x),  C(x) = 1 iff score(x) >= 1/2 sum_t alpha_t,
+ * h_t(x) = 1 iff p_t f_t(x) < p_t theta_t, f_t feature `stumps[t].feature` of
+ * vjb_enumerate_haar's list.  Sums are FP64 in stump order (both of them), so
+ * the result is that of the same sums done one by one on the host; a stump
+ * with alpha = +inf (a perfect stump) decides alone.  labels [n] receive
+ * C(x), scores [n] (may be NULL) the scores.  Needs vjb_enumerate_haar.
+ * Errors: VJB_EINVAL (a stump outside the feature list, polarity not +-1,
+ * NaN alpha), VJB_ESTATE, VJB_ENOMEM, VJB_ECUDA. */
+int vjb_classify(vjb_ctx *c, const uint8_t *pixels, int32_t n, const vjb_stump *stumps, int32_t T,
+                 uint8_t *labels, double *scores);
+
 /* ---- batches: many jobs per launch ------------------------------------------------
  * A batch trains many independent jobs (each its own windows, labels and
  * number of rounds) with one launch of each round kernel for all of them,

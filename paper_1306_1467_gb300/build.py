@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libvjb.so")
-SOURCES = ["vjb_api.cu", "k_prepare.cu", "k_search.cu", "k_update.cu"]
+SOURCES = ["vjb_api.cu", "k_prepare.cu", "k_search.cu", "k_update.cu", "k_classify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -789,6 +789,53 @@ int vjb_get_info(vjb_ctx *c, vjb_info *out) {
     return VJB_OK;
 }
 
+int vjb_classify(vjb_ctx *c, const uint8_t *pixels, int32_t n, const vjb_stump *stumps, int32_t T,
+                 uint8_t *labels, double *scores) {
+    g_err[0] = 0;
+    if (!c || !pixels || !labels || (T > 0 && !stumps)) return fail(VJB_EINVAL, "NULL argument");
+    if (c->stage < kStagePrepared) return fail(VJB_ESTATE, "vjb_classify before vjb_enumerate_haar");
+    if (n < 1 || n > (1 << 26)) return fail(VJB_EINVAL, "n = %d outside [1, 2^26]", n);
+    if (T < 0) return fail(VJB_EINVAL, "T < 0");
+    double half = 0.0;
+    for (int t = 0; t < T; ++t) {
+        const vjb_stump &s = stumps[t];
+        if (s.feature < 0 || s.feature >= c->nfeat || (s.polarity != 1 && s.polarity != -1) || std::isnan(s.alpha))
+            return fail(VJB_EINVAL, "stump %d is not a stump of this window size", t);
+        half += s.alpha;
+    }
+    half *= 0.5;  // C(x) = 1 iff sum alpha_t h_t(x) >= 1/2 sum alpha_t
+    int rc = set_dev(c);
+    if (rc) return rc;
+    const size_t px_bytes = (size_t)n * c->h * c->w;
+    const int stride = (n + 31) / 32 * 32;
+    uint8_t *d_px = nullptr, *d_lab = nullptr;
+    int32_t *d_ii = nullptr;
+    vjb_stump *d_st = nullptr;
+    double *d_sc = nullptr;
+    auto cleanup = [&]() {
+        dfree(d_px); dfree(d_lab); dfree(d_ii); dfree(d_st); dfree(d_sc);
+    };
+    cudaError_t e = cudaMalloc(&d_px, px_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&d_ii, sizeof(int32_t) * (size_t)(c->h + 1) * (c->w + 1) * stride);
+    if (e == cudaSuccess) e = cudaMalloc(&d_lab, (size_t)n);
+    if (e == cudaSuccess) e = cudaMalloc(&d_st, sizeof(vjb_stump) * (size_t)std::max(T, 1));
+    if (e == cudaSuccess && scores) e = cudaMalloc(&d_sc, sizeof(double) * (size_t)n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_px, pixels, px_bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess && T > 0) e = cudaMemcpyAsync(d_st, stumps, sizeof(vjb_stump) * T, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = launch_integral(d_px, n, c->h, c->w, d_ii, stride, c->stream);
+    if (e == cudaSuccess)
+        e = launch_strong_classify(d_ii, stride, n, c->w, c->d_feat, d_st, T, half, d_lab, d_sc, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(labels, d_lab, (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess && scores)
+        e = cudaMemcpyAsync(scores, d_sc, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    c->launches += 2;
+    cleanup();
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? VJB_ENOMEM : VJB_ECUDA, "classify: %s", cudaGetErrorString(e));
+    return VJB_OK;
+}
+
 int vjb_get_integral(vjb_ctx *c, int32_t *out) {
     g_err[0] = 0;
     if (!c || !out) return fail(VJB_EINVAL, "NULL argument");

@@ -178,6 +178,9 @@ WeightLayout make_layout(int n, bool allow_dual);
 // Launchers (each returns the launch error).
 cudaError_t launch_integral(const uint8_t *px, int n, int h, int w, int32_t *ii_t, int ii_stride,
                             cudaStream_t st);
+cudaError_t launch_strong_classify(const int32_t *ii_t, int ii_stride, int n, int win_w, const DevFeature *feat,
+                                   const vjb_stump *stumps, int T, double half_alpha, uint8_t *labels,
+                                   double *scores, cudaStream_t st);
 cudaError_t launch_feature_values(const int32_t *ii_t, int ii_stride, int n, int w,
                                   const DevFeature *feat, int64_t f0, int64_t nf, int32_t *out,
                                   cudaStream_t st);

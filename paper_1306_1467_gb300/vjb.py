@@ -141,6 +141,7 @@ SIGNATURES = {
     "vjb_force_stump": (C.c_int, [_P, _I32, _I32, _I32, _P]),
     "vjb_get_info": (C.c_int, [_P, _P]),
     "vjb_get_integral": (C.c_int, [_P, _P]),
+    "vjb_classify": (C.c_int, [_P, _P, _I32, _P, _I32, _P, _P]),
     "vjb_feature_values": (C.c_int, [_P, _I64, _I64, _P]),
     "vjb_sorted_rows": (C.c_int, [_P, _I64, _I64, _P]),
     "vjb_screen_errors": (C.c_int, [_P, _P]),
@@ -354,6 +355,21 @@ class Trainer:
         t = Timing()
         self._check(self._lib.vjb_get_timing(self._h, C.byref(t)))
         return t.as_dict()
+
+    # -- the strong classifier ----------------------------------------------------
+    def classify(self, pixels, stumps):
+        """C(x) and the FP64 scores of windows pixels [N, H, W] (host) under ``stumps``
+        (dicts as returned by train_round / train_strong)."""
+        px = np.ascontiguousarray(pixels, np.uint8)
+        n = px.shape[0]
+        arr = (Stump * max(len(stumps), 1))()
+        for t, s in enumerate(stumps):
+            for k, _ in Stump._fields_:
+                setattr(arr[t], k, s[k])
+        lab = np.zeros(n, np.uint8)
+        sc = np.zeros(n, np.float64)
+        self._check(self._lib.vjb_classify(self._h, _ptr(px), n, arr, len(stumps), _ptr(lab), _ptr(sc)))
+        return lab, sc
 
     # -- inspection -------------------------------------------------------------------
     def get_integral(self) -> np.ndarray:

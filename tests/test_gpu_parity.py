@@ -352,3 +352,34 @@ def test_precision_form_mid_size():
             assert abs(d["search_error"] - s["error"]) <= 1e-9 * s["error"]
             assert abs(d["screen_error"] - s["error"]) <= SCREEN_TOL
             assert d["screen_min"] <= d["screen_error"]
+
+
+def test_strong_classifier_matches_oracle(tiny_prepared):
+    """C(x) on held-out windows (Sec. 2.3, the final hypothesis): labels
+    bit-exact against the oracle, scores equal to the FP64 sums in stump
+    order; the training error of C falls as stumps are added."""
+    from paper_1306_1467_gb300 import vjb
+    px, y = synth.make_windows(150, 250, 10, 10, seed=4242)  # held-out, same generator
+    P = tiny_prepared
+    with _trainer() as tr:
+        tr.prepare(P.px, P.y)
+        st, stumps = tr.train_strong(10)
+        assert len(stumps) == 10
+        feats = P.desc[[s["feature"] for s in stumps]]
+        fval = O.feature_values(px, feats)
+        lab, sc = tr.classify(px, stumps)
+        assert np.array_equal(lab, O.strong_classify(fval, stumps))
+        ref = np.zeros(px.shape[0])
+        for t, s in enumerate(stumps):
+            h = fval[t] < s["threshold"] if s["polarity"] > 0 else fval[t] > s["threshold"]
+            ref = ref + np.where(h, s["alpha"], 0.0)
+        assert np.array_equal(sc, ref)
+        errs = [np.mean(tr.classify(P.px, stumps[:T])[0] != P.y) for T in (1, 3, 10)]
+        assert errs[2] <= errs[0]
+        # a perfect stump (alpha = +inf) decides alone
+        s0 = dict(stumps[0], alpha=math.inf)
+        lab_inf, _ = tr.classify(px, [s0] + stumps[1:3])
+        h0 = fval[0] < s0["threshold"] if s0["polarity"] > 0 else fval[0] > s0["threshold"]
+        assert np.array_equal(lab_inf, h0.astype(np.uint8))
+        with pytest.raises(vjb.VJBError):
+            tr.classify(px, [dict(stumps[0], feature=10 ** 7)])
