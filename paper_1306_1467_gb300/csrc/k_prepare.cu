@@ -403,8 +403,12 @@ static cudaError_t launch_sort_ipt(const int32_t *ii_t, int ii_stride, int w, co
 // has 9 bits (two passes cover an 18-bit span), and a CTA of 512 threads
 // needs about 100 KiB of shared memory, so two rows sort per SM at a time.
 // Only the value bits are sorted; the starting index order and stable passes
-// order ties by sample index.
+// order ties by sample index.  A pass ranks each item once: while the warps
+// count their digits, every item records its rank among its warp's earlier
+// items of the same digit (two 16-bit ranks per register), so the scatter
+// after the CTA-wide scan needs only the scanned offsets.
 constexpr int kPkThreads = 512;
+constexpr int kPkRefinePasses = 1;  // a second pass buys no search time
 constexpr int kPkWarps = kPkThreads / 32;
 constexpr int kPkDigitBits = 9;
 constexpr int kPkRadix = 1 << kPkDigitBits;
@@ -471,11 +475,22 @@ __global__ void __launch_bounds__(kPkThreads, 2)
         const int sh = ib + shift;
         for (int k = threadIdx.x; k < kPkHistWords; k += kPkThreads) hist[k] = 0;
         __syncthreads();
+        // each item's rank among the warp's earlier items of its digit, in
+        // position order (item j before item j + 1, lanes in order), two per word
+        uint32_t rk[(IPT + 1) / 2];
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const uint32_t dg = (c[j] >> sh) & (kPkRadix - 1);
             const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-            if (lane == __ffs(peers) - 1) hist[dg * kPkHistStride + wp] += __popc(peers);
+            const int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (lane == leader) {
+                old = hist[dg * kPkHistStride + wp];
+                hist[dg * kPkHistStride + wp] = old + __popc(peers);
+            }
+            old = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
+            if (j & 1) rk[j >> 1] |= old << 16;
+            else rk[j >> 1] = old;
         }
         __syncthreads();
         {
@@ -520,12 +535,7 @@ __global__ void __launch_bounds__(kPkThreads, 2)
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const uint32_t dg = (c[j] >> sh) & (kPkRadix - 1);
-            const uint32_t peers = __match_any_sync(0xffffffffu, dg);
-            const uint32_t base = hist[dg * kPkHistStride + wp];
-            __syncwarp();
-            if (lane == __ffs(peers) - 1) hist[dg * kPkHistStride + wp] = base + __popc(peers);
-            __syncwarp();
-            skey[base + __popc(peers & lt)] = c[j];
+            skey[hist[dg * kPkHistStride + wp] + ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = c[j];
         }
         __syncthreads();
 #pragma unroll
@@ -570,7 +580,7 @@ __global__ void __launch_bounds__(kPkThreads, 2)
                 if (level(bb) < level(ba)) { inc(bb); mask |= 1u << k; }
                 else inc(ba);
             }
-            for (int pass = 0; pass < 2; ++pass)
+            for (int pass = 0; pass < kPkRefinePasses; ++pass)
                 for (int k = 0; k < 32; ++k) {
                     const int p = k * run + g;
                     if (p >= n) break;

@@ -380,7 +380,7 @@ __device__ __forceinline__ Candidate cand_shfl_xor(const Candidate &c, int d) {
     return o;
 }
 
-constexpr int kRescanWarps = 8;
+constexpr int kRescanWarps = 32;  // one warp per lane run of the row
 
 struct RunResult {
     DF total, mx, mn;

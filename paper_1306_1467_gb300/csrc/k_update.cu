@@ -165,9 +165,33 @@ __device__ void update_a_block(const JobDesc &J, int blk) {
     cta_partials(mw, tw, below, J.partials, blk);
 }
 
-// Step 3-4, part 1, finish (one thread, after every block): the stump's FP64
-// error, threshold, beta and alpha, its record, and the update factors.
-__device__ void update_a_finish(const JobDesc &J, int nblocks) {
+// Sums of the three per-block partials over `nblocks` blocks, by the whole
+// finishing CTA in a fixed order (strided per thread, then the CTA); every
+// thread gets them.
+__device__ __forceinline__ void sum_partials(const double *partials, int nblocks, double &a, double &b,
+                                             double &c) {
+    __shared__ double red[3][kUpdateThreads / 32];
+    double x = 0.0, y = 0.0, z = 0.0;
+    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
+        x += ((volatile const double *)partials)[3 * k + 0];
+        y += ((volatile const double *)partials)[3 * k + 1];
+        z += ((volatile const double *)partials)[3 * k + 2];
+    }
+    x = warp_sum_d(x);
+    y = warp_sum_d(y);
+    z = warp_sum_d(z);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) { red[0][wp] = x; red[1][wp] = y; red[2][wp] = z; }
+    __syncthreads();
+    a = b = c = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += red[0][k]; b += red[1][k]; c += red[2][k]; }
+}
+
+// Step 3-4, part 1, finish (thread 0, after every block; the CTA's threads
+// have summed the partials): the stump's FP64 error, threshold, beta and
+// alpha, its record, and the update factors.
+__device__ void update_a_finish(const JobDesc &J, double M, double T, double B) {
     RoundState *rs = J.rs;
     const int n = J.lay.n;
     const bool forced = rs->forced != 0;
@@ -175,12 +199,6 @@ __device__ void update_a_finish(const JobDesc &J, int nblocks) {
     const int32_t p = forced ? rs->forced_polarity : rs->win_polarity;
     const int32_t s = forced ? 0 : rs->win_split;
     const DevFeature d = J.feat[f];
-    double M = 0.0, T = 0.0, B = 0.0;
-    for (int c = 0; c < nblocks; ++c) {
-        M += ((volatile double *)J.partials)[3 * c + 0];
-        T += ((volatile double *)J.partials)[3 * c + 1];
-        B += ((volatile double *)J.partials)[3 * c + 2];
-    }
     const double eps = M / T;
     int32_t theta, split = s;
     if (forced) {
@@ -257,31 +275,39 @@ __device__ void update_b_block(const JobDesc &J, int blk) {
     cta_partials(tp, tn, 0.0, J.partials, blk);
 }
 
-__device__ void update_b_finish(const JobDesc &J, int nblocks) {
+__device__ void update_b_finish(const JobDesc &J, double P, double Q) {
     RoundState *rs = J.rs;
-    double P = 0.0, Q = 0.0;
-    for (int c = 0; c < nblocks; ++c) {
-        P += ((volatile double *)J.partials)[3 * c + 0];
-        Q += ((volatile double *)J.partials)[3 * c + 1];
-    }
     rs->t_pos = P;
     rs->t_neg = Q;
     rs->weight_sum = P + Q;
     rs->done_update_b = 0u;
 }
 
+// The finishing CTA of update a / update b (all its threads).
+__device__ void finish_a(const JobDesc &J, int nblocks) {
+    double M, T, B;
+    sum_partials(J.partials, nblocks, M, T, B);
+    if (threadIdx.x == 0) update_a_finish(J, M, T, B);
+}
+
+__device__ void finish_b(const JobDesc &J, int nblocks) {
+    double P, Q, unused;
+    sum_partials(J.partials, nblocks, P, Q, unused);
+    if (threadIdx.x == 0) update_b_finish(J, P, Q);
+}
+
 __global__ void __launch_bounds__(kUpdateThreads) k_update_a(const JobDesc J) {
     if (J.rs->status != VJB_OK) return;
     update_a_block(J, blockIdx.x);
     if (!last_block_done(&J.rs->done_update_a, gridDim.x)) return;
-    if (threadIdx.x == 0) update_a_finish(J, gridDim.x);
+    finish_a(J, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kUpdateThreads) k_update_b(const JobDesc J) {
     if (J.rs->status != VJB_OK) return;
     update_b_block(J, blockIdx.x);
     if (!last_block_done(&J.rs->done_update_b, gridDim.x)) return;
-    if (threadIdx.x == 0) update_b_finish(J, gridDim.x);
+    finish_b(J, gridDim.x);
 }
 
 cudaError_t launch_update_a(const JobDesc &J, cudaStream_t st) {
@@ -318,9 +344,9 @@ __global__ void __launch_bounds__(kUpdateThreads) k_bupdate(const JobDesc *__res
         if (!J.rs->in_round || J.rs->status != VJB_OK) continue;
         if (A) update_a_block(J, blk);
         else update_b_block(J, blk);
-        if (last_block_done(A ? &J.rs->done_update_a : &J.rs->done_update_b, nblocks) && threadIdx.x == 0) {
-            if (A) update_a_finish(J, nblocks);
-            else update_b_finish(J, nblocks);
+        if (last_block_done(A ? &J.rs->done_update_a : &J.rs->done_update_b, nblocks)) {
+            if (A) finish_a(J, nblocks);
+            else finish_b(J, nblocks);
         }
         __syncthreads();
     }
