@@ -237,10 +237,10 @@ int vjb_screen_errors(vjb_ctx *ctx, float *out);
  * value.  Shapes whose shared memory does not fit one SM are rejected with
  * VJB_EINVAL.  Takes effect from the next round. */
 typedef struct {
-    int32_t warps;        /* consumer warps per CTA: 1-20 (1-12 with unroll 4)     */
+    int32_t warps;        /* consumer warps per CTA: 1-20 (1-16 unroll 3, 1-12 unroll 4) */
     int32_t stages;       /* TMA stages per warp: 1-8                              */
     int32_t ctas_per_sm;  /* 1-4                                                   */
-    int32_t unroll;       /* 16-entry pieces a lane works on together: 1, 2 or 4   */
+    int32_t unroll;       /* 16-entry pieces a lane works on together: 1-4         */
     int32_t box_lines;    /* 128-byte lines per TMA box (stage): 4-32, a multiple of 4 */
 } vjb_search_shape;
 
@@ -289,7 +289,7 @@ typedef struct vjb_batch vjb_batch;
 typedef struct {
     int32_t jobs;               /* jobs in the batch                                  */
     int32_t warps, stages, unroll, rows_per_warp;  /* search launch shape and schedule */
-    int32_t pad;
+    int32_t box_lines;          /* lines per TMA stage                                */
     int64_t budget_bytes;       /* the table arena                                    */
     int64_t free_bytes;         /* free arena                                         */
     int64_t largest_free_bytes; /* largest free block (the largest table that fits)   */
@@ -332,6 +332,7 @@ int vjb_batch_train(vjb_batch *b, int32_t max_rounds, int32_t *rounds_run);
  * number. */
 typedef struct {
     int32_t warps, stages, unroll, rows_per_warp;  /* the shape tried                  */
+    int32_t box_lines;                             /* lines per TMA stage              */
     float   ms_per_round;                          /* its timed rounds, on the device  */
 } vjb_batch_trial;
 int vjb_batch_autotune(vjb_batch *b, int32_t trial_rounds, int32_t *rounds_run, vjb_batch_trial *trials,
@@ -345,13 +346,15 @@ int vjb_batch_job_state(vjb_batch *b, int32_t job_id, int32_t *rounds_done, int3
 int vjb_batch_get_stumps(vjb_batch *b, int32_t job_id, int32_t first, int32_t count, vjb_stump *out);
 int vjb_batch_get_weights(vjb_batch *b, int32_t job_id, float *out);
 
-/* Launch shape of the batched search (box height is always 32 lines) and its
- * schedule: rows_per_warp > 0 hands out work items of that many features per
- * warp from a queue; VJB_BATCH_INTERLEAVED (the default) gives warp w of the
- * grid rows w, w + G, ... of every job in turn (G warps in the grid), the
- * plain search's order, with no barrier between a CTA's rows of one job.
- * A field or rows_per_warp of 0 keeps its value. */
-#define VJB_BATCH_INTERLEAVED (-1)
+/* Launch shape of the batched search (stage height box_lines: a multiple of 4
+ * up to 32 lines) and its schedule: rows_per_warp > 0 hands out work items of
+ * that many features per warp from a queue; VJB_BATCH_PARTITIONED (the
+ * default) gives each CTA one contiguous range of all jobs' rows, the same
+ * number of table lines for every CTA (recomputed each round for the jobs
+ * taking part), its warps taking every nw-th row, so a CTA synchronises only
+ * at the one or two job boundaries in its range.  A field or rows_per_warp of
+ * 0 keeps its value. */
+#define VJB_BATCH_PARTITIONED (-1)
 int vjb_batch_set_search_shape(vjb_batch *b, const vjb_search_shape *shape, int32_t rows_per_warp);
 int vjb_batch_get_info(vjb_batch *b, vjb_batch_info *out);
 

@@ -171,7 +171,7 @@ __device__ __forceinline__ float finish_row(float ahi, float alo, float bmx, flo
 }
 
 template <int U>
-__global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
+__global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
     k_screen(const __grid_constant__ CUtensorMap tmap, const float *__restrict__ v, int words,
              int lines_per_row, int box_lines, int stage_lines, int64_t nfeat,
              int stages, RoundState *rs, float *__restrict__ ferr, float *__restrict__ bmin) {
@@ -289,6 +289,10 @@ cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, const WeightL
         k_screen<4><<<grid, threads, sm, st>>>(*tmap, v, L.words, lines_per_row, box_lines,
                                                shape.box_lines, nfeat, shape.stages, rs, ferr, bmin);
         break;
+    case 3:
+        k_screen<3><<<grid, threads, sm, st>>>(*tmap, v, L.words, lines_per_row, box_lines,
+                                               shape.box_lines, nfeat, shape.stages, rs, ferr, bmin);
+        break;
     default:
         k_screen<2><<<grid, threads, sm, st>>>(*tmap, v, L.words, lines_per_row, box_lines,
                                                shape.box_lines, nfeat, shape.stages, rs, ferr, bmin);
@@ -299,11 +303,12 @@ cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, const WeightL
 cudaError_t set_screen_smem_limit(int bytes) {
     cudaError_t e = cudaFuncSetAttribute(k_screen<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_screen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_screen<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_screen<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     return e;
 }
 
-int screen_max_warps(int unroll) { return unroll >= 4 ? 12 : 20; }
+int screen_max_warps(int unroll) { return unroll >= 4 ? 12 : (unroll == 3 ? 16 : 20); }
 
 int screen_occupancy(const SearchShape &s, int words) {
     int blocks = 0;
@@ -311,6 +316,7 @@ int screen_occupancy(const SearchShape &s, int words) {
     const size_t sm = search_smem_bytes(s, words);
     if (s.unroll == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_screen<1>, s.warps * 32, sm);
     else if (s.unroll == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_screen<4>, s.warps * 32, sm);
+    else if (s.unroll == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_screen<3>, s.warps * 32, sm);
     else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_screen<2>, s.warps * 32, sm);
     return e == cudaSuccess ? blocks : 0;
 }
@@ -567,8 +573,23 @@ cudaError_t launch_rescan(const JobDesc &J, int grid, cudaStream_t st) {
 // of them.  The job table and the counters live in device memory, so a round
 // replays as one CUDA graph however the set of jobs changes between rounds.
 
-// Which jobs take part in this round; per-job search minimum reset.
+// Index of the job whose range [base_j, base_{j+1}) holds g (bases ascending).
+template <class F>
+__device__ __forceinline__ int find_job(int nj, int64_t g, F base) {
+    int lo = 0, hi = nj - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base(mid) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Which jobs take part in this round; per-job search minimum reset; the
+// partitioned search's row ranges.
 __global__ void k_bbegin(JobDesc *jobs, BatchMeta *meta) {
+    __shared__ int64_t cum[kMaxBatchJobs + 1];  // table lines (+1 per row) before each job
+    __shared__ int32_t rw[kMaxBatchJobs];       // lines + 1 of a row of each job taking part
     const int nj = meta->njobs;
     for (int j = threadIdx.x; j < nj; j += blockDim.x) {
         RoundState *rs = jobs[j].rs;
@@ -576,6 +597,35 @@ __global__ void k_bbegin(JobDesc *jobs, BatchMeta *meta) {
                        rs->rounds < jobs[j].round_target;
         rs->in_round = in;
         rs->screen_min_bits = 0x7f800000u;  // +inf
+        rw[j] = in ? jobs[j].lines + 1 : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int j = 0; j < nj; ++j) {
+            cum[j] = acc;
+            acc += (int64_t)rw[j] * jobs[j].nfeat;
+        }
+        cum[nj] = acc;
+    }
+    __syncthreads();
+    // CTA c starts at the row where the running count of lines reaches c / G
+    // of the whole; jobs that do not take part weigh nothing
+    const int G = meta->screen_ctas;
+    const int64_t W = cum[nj];
+    for (int c = threadIdx.x; c <= G; c += blockDim.x) {
+        int64_t g = meta->total_feat;
+        const int64_t target = W * c / G;
+        if (c < G && target < W) {
+            int lo = 0, hi = nj - 1;  // last job whose start is at or before the target
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (cum[mid] <= target) lo = mid;
+                else hi = mid - 1;
+            }
+            g = jobs[lo].feat_base + (target - cum[lo]) / rw[lo];
+        }
+        meta->cta_start[c] = g;
     }
 }
 
@@ -585,9 +635,7 @@ cudaError_t launch_bbegin(JobDesc *jobs, BatchMeta *meta, cudaStream_t st) {
 }
 
 size_t bscreen_smem_bytes(const SearchShape &s, int max_words) {
-    SearchShape t = s;
-    t.box_lines = kBoxLinesMax;  // batch stages always hold a whole 32-line chunk
-    return search_smem_bytes(t, max_words);
+    return search_smem_bytes(s, max_words);  // stages of s.box_lines lines
 }
 
 // Loads `lines_here` lines (a multiple of 4, at most 32) at `line` of the
@@ -613,13 +661,13 @@ __device__ __forceinline__ void load_lines(const BatchMaps &maps, uint32_t dst, 
 template <int U>
 __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     k_bscreen(const __grid_constant__ BatchMaps maps, const JobDesc *__restrict__ jobs,
-              const WorkItem *__restrict__ items, BatchMeta *meta, int max_words, int stages) {
+              const WorkItem *__restrict__ items, BatchMeta *meta, int max_words, int stages, int stage_lines) {
     extern __shared__ __align__(16) float sv[];
     __shared__ int s_item;
     __shared__ float s_min[32];
     const int nw = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t stage_bytes = kStageBytes;
+    const uint32_t stage_bytes = (uint32_t)stage_lines * kLineBytes;
     const uint32_t sv32 = smem_u32(sv);
     const uint32_t ring0 = (uint32_t)align_up(sv32 + (uint32_t)max_words * 4u, 1024);
     const uint32_t bars0 = ring0 + (uint32_t)nw * stages * stage_bytes;
@@ -650,7 +698,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
             cur_job = W.job;
         }
         const int lines = J.lines;
-        const int nc = (lines + kBoxLinesMax - 1) / kBoxLinesMax;
+        const int nc = (lines + stage_lines - 1) / stage_lines;
         const int nrows = W.f1 - W.f0 > warp ? (W.f1 - W.f0 - warp + nw - 1) / nw : 0;
         const int total = ok ? nrows * nc : 0;
         const float Tp = (float)J.rs->t_pos, Tm = (float)J.rs->t_neg;
@@ -659,9 +707,9 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
         auto issue_next = [&]() {
             if (issued >= total) return;
             const int64_t f = W.f0 + warp + (int64_t)pk * nw;
-            const int lh = min(kBoxLinesMax, lines - pc * kBoxLinesMax);
+            const int lh = min(stage_lines, lines - pc * stage_lines);
             load_lines(maps, ring_w + (uint32_t)pstage * stage_bytes,
-                       J.line_base + f * lines + (int64_t)pc * kBoxLinesMax, lh, bar_w + 8u * (uint32_t)pstage);
+                       J.line_base + f * lines + (int64_t)pc * stage_lines, lh, bar_w + 8u * (uint32_t)pstage);
             if (++pc == nc) { pc = 0; ++pk; }
             if (++pstage == stages) pstage = 0;
             ++issued;
@@ -679,7 +727,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
                     ok = false;
                     break;
                 }
-                const int lh = min(kBoxLinesMax, lines - c * kBoxLinesMax);
+                const int lh = min(stage_lines, lines - c * stage_lines);
                 scan_stage<U>(ring_w + (uint32_t)cstage * stage_bytes, lh >> 2, lane, sv, ahi, alo, bmx, bmn);
                 __syncwarp();
                 if (lane == 0) {
@@ -726,21 +774,21 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     }
 }
 
-// Interleaved schedule: the plain kernel's row order applied to every job in
-// turn.  Warp w of the grid takes rows w, w + G, w + 2G, ... (G warps in the
-// grid) of job 0, then of job 1, and so on; its producer lane runs ahead
-// across job boundaries, so the TMA ring never drains.  The CTA synchronises
-// only when it moves to the next job (to swap the weights in shared memory),
-// and skips jobs in which none of its warps has a row.
+// Partitioned schedule: CTA c takes one contiguous range of all jobs' rows
+// (job after job), sized by k_bbegin so that every CTA streams the same number
+// of table lines; inside it, warp w takes every nw-th row of each job, and its
+// producer lane runs ahead across job boundaries so the TMA ring never drains.
+// The CTA synchronises only when it moves to the next job (to swap the weights
+// in shared memory), which with ranges this long happens once or twice a round.
 template <int U>
 __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
-    k_bscreen_il(const __grid_constant__ BatchMaps maps, const JobDesc *__restrict__ jobs,
-                 BatchMeta *meta, int max_words, int stages) {
+    k_bscreen_pt(const __grid_constant__ BatchMaps maps, const JobDesc *__restrict__ jobs,
+                 BatchMeta *meta, int max_words, int stages, int stage_lines) {
     extern __shared__ __align__(16) float sv[];
     __shared__ float s_min[32];
     const int nw = blockDim.x >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t stage_bytes = kStageBytes;
+    const uint32_t stage_bytes = (uint32_t)stage_lines * kLineBytes;
     const uint32_t sv32 = smem_u32(sv);
     const uint32_t ring0 = (uint32_t)align_up(sv32 + (uint32_t)max_words * 4u, 1024);
     const uint32_t bars0 = ring0 + (uint32_t)nw * stages * stage_bytes;
@@ -751,33 +799,45 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
         fence_barrier_init();
     }
     const int nj = meta->njobs;
-    const int64_t gw = (int64_t)blockIdx.x * nw + warp;
-    const int64_t G = (int64_t)gridDim.x * nw;
-    auto rows_of = [&](const JobDesc &J) -> int64_t {
-        return (J.rs->in_round && gw < J.nfeat) ? (J.nfeat - 1 - gw) / G + 1 : 0;
+    const int64_t g0 = meta->cta_start[blockIdx.x], g1 = meta->cta_start[blockIdx.x + 1];
+    // first job of the range
+    const int j0 = find_job(nj, g0, [&](int i) { return jobs[i].feat_base; });
+    // the CTA's rows of job J: [a, b); this warp's: a + warp, a + warp + nw, ...
+    auto range_of = [&](const JobDesc &J, int64_t &a, int64_t &b) {
+        a = max(g0 - J.feat_base, (int64_t)0);
+        b = min(g1 - J.feat_base, J.nfeat);
+        if (!J.rs->in_round || a >= b) a = b = 0;
+    };
+    auto rows_of = [&](int64_t a, int64_t b) -> int64_t {
+        return b - a > warp ? (b - a - warp + nw - 1) / nw : 0;
     };
     // producer (lane 0): job, row and chunk of the next load, in this warp's order
-    int pj = -1, pc = 0, pstage = 0, p_nc = 0, p_lines = 0;
-    int64_t pk = 0, p_rows = 0, p_base = 0, issued = 0;
+    int pj = j0 - 1, pc = 0, pstage = 0, p_nc = 0, p_lines = 0;
+    int64_t pk = 0, p_rows = 0, p_first = 0, p_base = 0, issued = 0;
     auto next_job = [&]() {
-        for (++pj; pj < nj; ++pj) {
+        for (++pj; pj < nj && jobs[pj].feat_base < g1; ++pj) {
             const JobDesc &J = jobs[pj];
-            p_rows = rows_of(J);
+            int64_t a, b;
+            range_of(J, a, b);
+            p_rows = rows_of(a, b);
             if (p_rows) {
+                p_first = a + warp;
                 p_lines = J.lines;
-                p_nc = (p_lines + kBoxLinesMax - 1) / kBoxLinesMax;
+                p_nc = (p_lines + stage_lines - 1) / stage_lines;
                 p_base = J.line_base;
                 pk = 0;
                 pc = 0;
                 return;
             }
         }
+        pj = nj;
     };
     auto issue_next = [&]() {
         if (pj >= nj) return;
-        const int lh = min(kBoxLinesMax, p_lines - pc * kBoxLinesMax);
+        const int lh = min(stage_lines, p_lines - pc * stage_lines);
         load_lines(maps, ring_w + (uint32_t)pstage * stage_bytes,
-                   p_base + (gw + pk * G) * p_lines + (int64_t)pc * kBoxLinesMax, lh, bar_w + 8u * (uint32_t)pstage);
+                   p_base + (p_first + pk * nw) * p_lines + (int64_t)pc * stage_lines, lh,
+                   bar_w + 8u * (uint32_t)pstage);
         if (++pstage == stages) pstage = 0;
         ++issued;
         if (++pc == p_nc) {
@@ -794,9 +854,11 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     uint32_t cpar = 0;
     int64_t consumed = 0;
     bool ok = true;  // false once one of this warp's waits timed out
-    for (int j = 0; j < nj; ++j) {
+    for (int j = j0; j < nj && jobs[j].feat_base < g1; ++j) {
         const JobDesc &J = jobs[j];
-        if (!J.rs->in_round || (int64_t)blockIdx.x * nw >= J.nfeat) continue;  // uniform over the CTA
+        int64_t a, b;
+        range_of(J, a, b);
+        if (a >= b) continue;  // uniform over the CTA
         __syncthreads();  // every warp is done with the previous job's weights and minima
         if (prev >= 0 && threadIdx.x == 0) {
             float m = INFINITY;
@@ -807,19 +869,20 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
         __syncthreads();
         prev = j;
         const int lines = J.lines;
-        const int nc = (lines + kBoxLinesMax - 1) / kBoxLinesMax;
-        const int64_t nrows = ok ? rows_of(J) : 0;
+        const int nc = (lines + stage_lines - 1) / stage_lines;
+        const int64_t nrows = ok ? rows_of(a, b) : 0;
         const float Tp = (float)J.rs->t_pos, Tm = (float)J.rs->t_neg;
+        float *ferr = J.ferr;
         float wmin = INFINITY;
         for (int64_t k = 0; k < nrows && ok; ++k) {
-            const int64_t f = gw + k * G;
+            const int64_t f = a + warp + k * nw;
             float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
             for (int c = 0; c < nc; ++c) {
                 if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
                     ok = false;
                     break;
                 }
-                const int lh = min(kBoxLinesMax, lines - c * kBoxLinesMax);
+                const int lh = min(stage_lines, lines - c * stage_lines);
                 scan_stage<U>(ring_w + (uint32_t)cstage * stage_bytes, lh >> 2, lane, sv, ahi, alo, bmx, bmn);
                 __syncwarp();
                 if (lane == 0) {
@@ -831,7 +894,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
             }
             if (!ok) break;
             const float e = finish_row(ahi, alo, bmx, bmn, Tp, Tm, lane);
-            if (lane == 0) J.ferr[f] = e;
+            if (lane == 0) ferr[f] = e;
             wmin = fminf(wmin, e);
         }
         if (!ok && lane == 0) {
@@ -857,47 +920,45 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
 }
 
 cudaError_t launch_bscreen(const BatchMaps &maps, const JobDesc *jobs, const WorkItem *items,
-                           BatchMeta *meta, int max_words, const SearchShape &shape, bool interleaved,
+                           BatchMeta *meta, int max_words, const SearchShape &shape, bool partitioned,
                            int grid, cudaStream_t st) {
     const size_t sm = bscreen_smem_bytes(shape, max_words);
     const int threads = shape.warps * 32;
-    if (interleaved) {
+    const int sl = shape.box_lines;
+    if (partitioned) {
         switch (shape.unroll) {
-        case 1: k_bscreen_il<1><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages); break;
-        case 4: k_bscreen_il<4><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages); break;
-        default: k_bscreen_il<2><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages);
+        case 1: k_bscreen_pt<1><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages, sl); break;
+        case 3: k_bscreen_pt<3><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages, sl); break;
+        case 4: k_bscreen_pt<4><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages, sl); break;
+        default: k_bscreen_pt<2><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages, sl);
         }
         return cudaGetLastError();
     }
     switch (shape.unroll) {
-    case 1: k_bscreen<1><<<grid, threads, sm, st>>>(maps, jobs, items, meta, max_words, shape.stages); break;
-    case 4: k_bscreen<4><<<grid, threads, sm, st>>>(maps, jobs, items, meta, max_words, shape.stages); break;
-    default: k_bscreen<2><<<grid, threads, sm, st>>>(maps, jobs, items, meta, max_words, shape.stages);
+    case 1: k_bscreen<1><<<grid, threads, sm, st>>>(maps, jobs, items, meta, max_words, shape.stages, sl); break;
+    case 3: k_bscreen<3><<<grid, threads, sm, st>>>(maps, jobs, items, meta, max_words, shape.stages, sl); break;
+    case 4: k_bscreen<4><<<grid, threads, sm, st>>>(maps, jobs, items, meta, max_words, shape.stages, sl); break;
+    default: k_bscreen<2><<<grid, threads, sm, st>>>(maps, jobs, items, meta, max_words, shape.stages, sl);
     }
     return cudaGetLastError();
 }
 
 cudaError_t set_bscreen_smem_limit(int bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_bscreen<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bscreen<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bscreen<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bscreen_il<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bscreen_il<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_bscreen_il<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaSuccess;
+    auto set = [&](const void *fn) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    };
+    set((const void *)k_bscreen<1>);
+    set((const void *)k_bscreen<2>);
+    set((const void *)k_bscreen<3>);
+    set((const void *)k_bscreen<4>);
+    set((const void *)k_bscreen_pt<1>);
+    set((const void *)k_bscreen_pt<2>);
+    set((const void *)k_bscreen_pt<3>);
+    set((const void *)k_bscreen_pt<4>);
     return e;
 }
 
-// Index of the job whose range [base_j, base_{j+1}) holds g (bases ascending).
-template <class F>
-__device__ __forceinline__ int find_job(int nj, int64_t g, F base) {
-    int lo = 0, hi = nj - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (base(mid) <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
-}
 
 __global__ void __launch_bounds__(256) k_bshortlist(const JobDesc *__restrict__ jobs, BatchMeta *meta) {
     __shared__ int64_t base[kMaxBatchJobs];

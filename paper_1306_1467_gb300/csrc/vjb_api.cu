@@ -224,9 +224,9 @@ int apply_shape(vjb_ctx *c) {
 
 int choose_default_shape(vjb_ctx *c) {
     if (c->shape_set && shape_fits(c, c->shape)) return apply_shape(c);
-    // measured on the 24x24 / 15k workload: as many warps as shared memory allows,
-    // two stages of 4 KiB, four pieces in flight per lane
-    const SearchShape tries[] = {{12, 2, 1, 4, 32}, {12, 2, 1, 2, 32}, {16, 2, 1, 2, 24}, {8, 3, 1, 4, 32},
+    // measured on the 24x24 / 15k workload: 16 warps (four per scheduler), two
+    // stages of 24 lines, three pieces in flight per lane; then smaller shapes
+    const SearchShape tries[] = {{16, 2, 1, 3, 24}, {12, 2, 1, 4, 32}, {12, 2, 1, 2, 32}, {8, 3, 1, 4, 32},
                                  {8, 2, 1, 4, 32}, {6, 3, 1, 2, 32}, {4, 4, 1, 2, 32}, {4, 2, 1, 2, 32},
                                  {2, 2, 1, 2, 16}, {2, 2, 1, 1, 8}};
     for (const auto &s : tries)
@@ -913,7 +913,7 @@ int vjb_set_search_shape(vjb_ctx *c, const vjb_search_shape *in) {
     if (in->unroll) s.unroll = in->unroll;
     if (in->box_lines) s.box_lines = in->box_lines;
     if (s.warps < 1 || s.warps > 20 || s.stages < 1 || s.stages > 8 || s.ctas_per_sm < 1 || s.ctas_per_sm > 4 ||
-        (s.unroll != 1 && s.unroll != 2 && s.unroll != 4) || s.warps > screen_max_warps(s.unroll) ||
+        (s.unroll < 1 || s.unroll > 4) || s.warps > screen_max_warps(s.unroll) ||
         s.box_lines < 4 || s.box_lines > 32 || s.box_lines % 4 != 0)
         return fail(VJB_EINVAL, "search shape (%d warps, %d stages, %d CTAs/SM, unroll %d, box %d lines) out of range",
                     s.warps, s.stages, s.ctas_per_sm, s.unroll, s.box_lines);
@@ -1020,8 +1020,8 @@ struct vjb_batch {
     WorkItem *d_items = nullptr;
     int items_cap = 0;
     bool dirty = true;  // the device job table must be rebuilt
-    SearchShape shape{12, 2, 1, 4, 32};
-    int rows_per_warp = VJB_BATCH_INTERLEAVED;  // > 0: work queue of that many rows per warp and item
+    SearchShape shape{16, 2, 1, 3, 24};
+    int rows_per_warp = VJB_BATCH_PARTITIONED;  // > 0: work queue of that many rows per warp and item
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t launches = 0;
@@ -1137,6 +1137,7 @@ int batch_sync(vjb_batch *b) {
     if (!items.empty())
         CK(cudaMemcpyAsync(b->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, b->stream));
     BatchMeta m{};
+    m.screen_ctas = b->num_sms * b->shape.ctas_per_sm;
     m.njobs = nj;
     m.n_items = (int32_t)items.size();
     m.total_feat = fbase;
@@ -1241,7 +1242,8 @@ int batch_ensure_graph(vjb_batch *b) {
 
 bool batch_shape_ok(const vjb_batch *b, const SearchShape &s) {
     return s.warps >= 1 && s.warps <= screen_max_warps(s.unroll) && s.stages >= 1 && s.stages <= 8 &&
-           s.ctas_per_sm == 1 && (s.unroll == 1 || s.unroll == 2 || s.unroll == 4) &&
+           s.ctas_per_sm == 1 && s.unroll >= 1 && s.unroll <= 4 && s.box_lines >= 4 &&
+           s.box_lines <= kBoxLinesMax && s.box_lines % 4 == 0 &&
            bscreen_smem_bytes(s, kBatchMaxWords) + 256 <= (size_t)b->max_smem;
 }
 
@@ -1486,10 +1488,10 @@ int vjb_batch_autotune(vjb_batch *b, int32_t trial_rounds, int32_t *rounds_run, 
     CK(cudaSetDevice(b->device));
     // (warps, stages, unroll, features per warp and work item); results do not
     // depend on the shape, so every trial round is a real round of the jobs
-    // (rows VJB_BATCH_INTERLEAVED: the interleaved schedule, else the work queue)
-    constexpr int IL = VJB_BATCH_INTERLEAVED;
-    static const int kTries[][4] = {{12, 2, 4, IL}, {10, 2, 4, IL}, {8, 3, 4, IL}, {6, 4, 4, IL},
-                                    {16, 1, 2, IL}, {12, 2, 2, IL}, {12, 2, 4, 16}, {12, 2, 4, 32}};
+    // (rows VJB_BATCH_PARTITIONED: the partitioned schedule, else the work queue)
+    constexpr int IL = VJB_BATCH_PARTITIONED;
+    static const int kTries[][5] = {{16, 2, 3, 24, IL}, {12, 2, 4, 32, IL}, {16, 2, 3, 24, 16}, {16, 2, 3, 24, 32},
+                                    {12, 2, 4, 32, 32}, {8, 3, 4, 32, IL},  {16, 2, 2, 16, IL}, {8, 2, 3, 24, IL}};
     const SearchShape keep = b->shape;
     const int keep_rpw = b->rows_per_warp;
     double best = -1.0;
@@ -1500,10 +1502,10 @@ int vjb_batch_autotune(vjb_batch *b, int32_t trial_rounds, int32_t *rounds_run, 
         int rc = batch_rounds_wanted(b, &want);
         if (rc) return rc;
         if (want < trial_rounds + 1) break;
-        const SearchShape s{t[0], t[1], 1, t[2], kBoxLinesMax};
+        const SearchShape s{t[0], t[1], 1, t[2], t[3]};
         if (!batch_shape_ok(b, s)) continue;
         b->shape = s;
-        b->rows_per_warp = t[3];
+        b->rows_per_warp = t[4];
         b->dirty = true;
         b->drop_graph();
         float ms = 0.f;
@@ -1512,12 +1514,12 @@ int vjb_batch_autotune(vjb_batch *b, int32_t trial_rounds, int32_t *rounds_run, 
         if (rc) return rc;
         ran += 1 + trial_rounds;
         if (trials && ntr < max_trials)
-            trials[ntr] = vjb_batch_trial{s.warps, s.stages, s.unroll, t[3], ms / (float)trial_rounds};
+            trials[ntr] = vjb_batch_trial{s.warps, s.stages, s.unroll, t[4], s.box_lines, ms / (float)trial_rounds};
         ++ntr;
         if (best < 0.0 || ms < best) {
             best = ms;
             best_s = s;
-            best_rpw = t[3];
+            best_rpw = t[4];
         }
     }
     b->shape = best_s;
@@ -1575,9 +1577,9 @@ int vjb_batch_set_search_shape(vjb_batch *b, const vjb_search_shape *in, int32_t
         if (in->stages) s.stages = in->stages;
         if (in->unroll) s.unroll = in->unroll;
         if (in->ctas_per_sm) s.ctas_per_sm = in->ctas_per_sm;
+        if (in->box_lines) s.box_lines = in->box_lines;
     }
-    s.box_lines = kBoxLinesMax;
-    if (!batch_shape_ok(b, s) || rows_per_warp < VJB_BATCH_INTERLEAVED || rows_per_warp > 4096)
+    if (!batch_shape_ok(b, s) || rows_per_warp < VJB_BATCH_PARTITIONED || rows_per_warp > 4096)
         return fail(VJB_EINVAL, "batch search shape (%d warps, %d stages, unroll %d, %d rows per warp) not usable",
                     s.warps, s.stages, s.unroll, rows_per_warp);
     b->shape = s;
@@ -1595,6 +1597,7 @@ int vjb_batch_get_info(vjb_batch *b, vjb_batch_info *out) {
     out->warps = b->shape.warps;
     out->stages = b->shape.stages;
     out->unroll = b->shape.unroll;
+    out->box_lines = b->shape.box_lines;
     out->rows_per_warp = b->rows_per_warp;
     out->budget_bytes = b->arena_lines * kLineBytes;
     int64_t free_lines = 0, largest = 0;

@@ -147,6 +147,7 @@ struct JobDesc {
 };
 
 // Batch-wide counters in device memory.
+constexpr int kMaxScreenCtas = 1024;
 struct BatchMeta {
     int32_t njobs;          // job slots in use
     int32_t n_items;        // search work items
@@ -155,6 +156,12 @@ struct BatchMeta {
     int64_t total_feat;     // sum of nfeat over the job slots
     int32_t total_ublocks;  // sum of update blocks over the job slots
     int32_t flags;          // error flags of batched kernels
+    int32_t screen_ctas;    // CTAs of the partitioned search
+    int32_t pad;
+    // partitioned search: CTA c takes rows [cta_start[c], cta_start[c + 1]) of
+    // the jobs' rows in job order (row g of job j is g - feat_base_j), set each
+    // round by k_bbegin so that every CTA gets the same share of table lines
+    int64_t cta_start[kMaxScreenCtas + 1];
 };
 
 // A search work item: features [f0, f1) of one job.
@@ -204,7 +211,7 @@ struct BatchMaps {
 };
 cudaError_t launch_bbegin(JobDesc *jobs, BatchMeta *meta, cudaStream_t st);
 cudaError_t launch_bscreen(const BatchMaps &maps, const JobDesc *jobs, const WorkItem *items,
-                           BatchMeta *meta, int max_words, const SearchShape &shape, bool interleaved,
+                           BatchMeta *meta, int max_words, const SearchShape &shape, bool partitioned,
                            int grid, cudaStream_t st);
 cudaError_t launch_bshortlist(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st);
 cudaError_t launch_brescan(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st);

@@ -22,7 +22,7 @@ OK, DONE_PERFECT, DONE_NOGAIN = 0, 1, 2
 EINVAL, ESTATE, ENOMEM, ECUDA, EDEVICE, EFULL = -1, -2, -3, -4, -5, -6
 MAX_SAMPLES = 32766
 REQ_QUEUED, REQ_PREPARING, REQ_TRAINING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3, 4
-BATCH_INTERLEAVED = -1
+BATCH_PARTITIONED = -1
 HAAR_TYPES = ("3H", "3V", "2H", "2V", "4")
 
 
@@ -87,7 +87,7 @@ class Timing(C.Structure):
 
 class BatchInfo(C.Structure):
     _fields_ = [("jobs", C.c_int32), ("warps", C.c_int32), ("stages", C.c_int32), ("unroll", C.c_int32),
-                ("rows_per_warp", C.c_int32), ("pad", C.c_int32), ("budget_bytes", C.c_int64),
+                ("rows_per_warp", C.c_int32), ("box_lines", C.c_int32), ("budget_bytes", C.c_int64),
                 ("free_bytes", C.c_int64), ("largest_free_bytes", C.c_int64),
                 ("search_bytes", C.c_double), ("launches", C.c_int64)]
 
@@ -97,7 +97,7 @@ class BatchInfo(C.Structure):
 
 class BatchTrial(C.Structure):
     _fields_ = [("warps", C.c_int32), ("stages", C.c_int32), ("unroll", C.c_int32),
-                ("rows_per_warp", C.c_int32), ("ms_per_round", C.c_float)]
+                ("rows_per_warp", C.c_int32), ("box_lines", C.c_int32), ("ms_per_round", C.c_float)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -492,10 +492,11 @@ class Batch:
         self._check(self._lib.vjb_batch_get_weights(self._h, int(job_id), _ptr(out)))
         return out
 
-    def set_search_shape(self, warps: int = 0, stages: int = 0, unroll: int = 0, rows_per_warp: int = 0):
+    def set_search_shape(self, warps: int = 0, stages: int = 0, unroll: int = 0, rows_per_warp: int = 0,
+                         box_lines: int = 0):
         """Batched search launch shape; rows_per_warp > 0 selects the work queue with that many
-        features per warp and item, BATCH_INTERLEAVED the interleaved schedule, 0 keeps it."""
-        sh = SearchShapeC(int(warps), int(stages), 0, int(unroll), 0)
+        features per warp and item, BATCH_PARTITIONED the partitioned schedule, 0 keeps a field."""
+        sh = SearchShapeC(int(warps), int(stages), 0, int(unroll), int(box_lines))
         self._check(self._lib.vjb_batch_set_search_shape(self._h, C.byref(sh), int(rows_per_warp)))
 
     def info(self) -> dict:

@@ -106,7 +106,7 @@ def test_batch_jobs_change_between_calls():
         b.remove_job(a)
         c = b.add_job(*jc, rounds=5)
         assert b.train(2) == 2
-        assert b.info()["rows_per_warp"] == vjb.BATCH_INTERLEAVED
+        assert b.info()["rows_per_warp"] == vjb.BATCH_PARTITIONED
         b.set_search_shape(warps=8, stages=3, rows_per_warp=4)  # work queue; results do not depend on it
         b.train()
         _same(b, bb, *jb, 10)
