@@ -505,8 +505,8 @@ def batch_comparison(a, device: int = 0) -> dict:
                         "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_source": f"{peak_src} hbm_gbs",
                         "rounds_timed": rest, "autotune_rounds": tuned,
                         "shape": {**{k: info[k] for k in ("warps", "stages", "unroll")},
-                                  "schedule": ("partitioned" if info["rows_per_warp"] < 0 else
-                                               f"work queue, {info['rows_per_warp']} rows per warp and item")},
+                                  "schedule": {-1: "partitioned", -2: "interleaved"}.get(
+                                      info["rows_per_warp"], f"work queue, {info['rows_per_warp']} rows per warp and item")},
                         "setup_s": setup_s, "launches_per_round": 6,
                         "roofline": {"kernel": "k_bscreen", "bound": "hbm", "achieved": search_gbs, "peak": peak,
                                      "unit": "GB/s", "frac": search_gbs / peak,

@@ -347,14 +347,19 @@ int vjb_batch_get_stumps(vjb_batch *b, int32_t job_id, int32_t first, int32_t co
 int vjb_batch_get_weights(vjb_batch *b, int32_t job_id, float *out);
 
 /* Launch shape of the batched search (stage height box_lines: a multiple of 4
- * up to 32 lines) and its schedule: rows_per_warp > 0 hands out work items of
- * that many features per warp from a queue; VJB_BATCH_PARTITIONED (the
- * default) gives each CTA one contiguous range of all jobs' rows, the same
- * number of table lines for every CTA (recomputed each round for the jobs
- * taking part), its warps taking every nw-th row, so a CTA synchronises only
- * at the one or two job boundaries in its range.  A field or rows_per_warp of
- * 0 keeps its value. */
+ * up to 32 lines) and its schedule (rows_per_warp):
+ *  - VJB_BATCH_INTERLEAVED (the default): the plain search's row order, one
+ *    job after the other: warp w of the grid's G warps takes rows w, w + G, ...
+ *    so the whole GPU streams one compact window of consecutive rows; a CTA
+ *    synchronises at every job;
+ *  - VJB_BATCH_PARTITIONED: each CTA takes one contiguous range of all jobs'
+ *    rows with the same number of table lines (recomputed each round for the
+ *    jobs taking part), so it synchronises once or twice a round;
+ *  - > 0: a queue of work items of that many rows per warp.
+ * Results do not depend on the choice.  A field or rows_per_warp of 0 keeps
+ * its value. */
 #define VJB_BATCH_PARTITIONED (-1)
+#define VJB_BATCH_INTERLEAVED (-2)
 int vjb_batch_set_search_shape(vjb_batch *b, const vjb_search_shape *shape, int32_t rows_per_warp);
 int vjb_batch_get_info(vjb_batch *b, vjb_batch_info *out);
 

@@ -638,24 +638,18 @@ size_t bscreen_smem_bytes(const SearchShape &s, int max_words) {
     return search_smem_bytes(s, max_words);  // stages of s.box_lines lines
 }
 
-// Loads `lines_here` lines (a multiple of 4, at most 32) at `line` of the
-// arena into a stage, as boxes of 32, 16, 8 and 4 lines, all completing on `bar`.
-__device__ __forceinline__ void load_lines(const BatchMaps &maps, uint32_t dst, int64_t line,
-                                           int lines_here, uint32_t bar) {
-    mbar_arrive_expect_tx(bar, (uint32_t)lines_here * kLineBytes);
-    int done = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const int box = kBoxLinesMax >> b;
-        if (lines_here - done >= box) {
-            asm volatile(
-                "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst + (uint32_t)done * kLineBytes),
-                "l"(reinterpret_cast<uint64_t>(&maps.m[b])), "r"(0), "r"((int32_t)(line + done)), "r"(bar)
-                : "memory");
-            done += box;
-        }
-    }
+// One stage of the batched search: `lh` lines (a multiple of 4, at most the
+// stage height S) at arena line `line`, with one copy from the map whose box
+// is exactly that height, completing on `bar`.
+__device__ __forceinline__ void tma_stage(const BatchMaps &maps, uint32_t dst, int32_t line, int lh, int S,
+                                          uint32_t bar) {
+    mbar_arrive_expect_tx(bar, (uint32_t)lh * kLineBytes);
+    const CUtensorMap *m = &maps.m[lh == S ? 0 : (lh >> 2)];
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(0), "r"(line), "r"(bar)
+        : "memory");
 }
 
 template <int U>
@@ -702,15 +696,21 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
         const int nrows = W.f1 - W.f0 > warp ? (W.f1 - W.f0 - warp + nw - 1) / nw : 0;
         const int total = ok ? nrows * nc : 0;
         const float Tp = (float)J.rs->t_pos, Tm = (float)J.rs->t_neg;
-        // producer (lane 0) position inside this item
-        int pk = 0, pc = 0, issued = 0;
+        // producer (lane 0): the arena line of the next stage and the lines left in its row
+        int issued = 0, p_left = lines;
+        int64_t p_row = J.line_base + (W.f0 + warp) * (int64_t)lines, p_cur = p_row;
+        const int64_t p_step = (int64_t)nw * lines;
         auto issue_next = [&]() {
             if (issued >= total) return;
-            const int64_t f = W.f0 + warp + (int64_t)pk * nw;
-            const int lh = min(stage_lines, lines - pc * stage_lines);
-            load_lines(maps, ring_w + (uint32_t)pstage * stage_bytes,
-                       J.line_base + f * lines + (int64_t)pc * stage_lines, lh, bar_w + 8u * (uint32_t)pstage);
-            if (++pc == nc) { pc = 0; ++pk; }
+            const int lh = min(stage_lines, p_left);
+            tma_stage(maps, ring_w + (uint32_t)pstage * stage_bytes, (int32_t)p_cur, lh, stage_lines,
+                      bar_w + 8u * (uint32_t)pstage);
+            p_cur += lh;
+            if ((p_left -= lh) == 0) {
+                p_row += p_step;
+                p_cur = p_row;
+                p_left = lines;
+            }
             if (++pstage == stages) pstage = 0;
             ++issued;
         };
@@ -811,9 +811,11 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     auto rows_of = [&](int64_t a, int64_t b) -> int64_t {
         return b - a > warp ? (b - a - warp + nw - 1) / nw : 0;
     };
-    // producer (lane 0): job, row and chunk of the next load, in this warp's order
-    int pj = j0 - 1, pc = 0, pstage = 0, p_nc = 0, p_lines = 0;
-    int64_t pk = 0, p_rows = 0, p_first = 0, p_base = 0, issued = 0;
+    // producer (lane 0): job of the next load, the arena line of its stage, the
+    // lines left in its row and the rows left in the job, in this warp's order
+    int pj = j0 - 1, pstage = 0, p_lines = 0, p_left = 0;
+    int32_t p_row = 0, p_cur = 0, p_step = 0;
+    int64_t p_rows = 0, issued = 0;
     auto next_job = [&]() {
         for (++pj; pj < nj && jobs[pj].feat_base < g1; ++pj) {
             const JobDesc &J = jobs[pj];
@@ -821,12 +823,11 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
             range_of(J, a, b);
             p_rows = rows_of(a, b);
             if (p_rows) {
-                p_first = a + warp;
                 p_lines = J.lines;
-                p_nc = (p_lines + stage_lines - 1) / stage_lines;
-                p_base = J.line_base;
-                pk = 0;
-                pc = 0;
+                p_left = p_lines;
+                p_row = (int32_t)(J.line_base + (a + warp) * (int64_t)p_lines);
+                p_cur = p_row;
+                p_step = nw * p_lines;
                 return;
             }
         }
@@ -834,15 +835,20 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     };
     auto issue_next = [&]() {
         if (pj >= nj) return;
-        const int lh = min(stage_lines, p_lines - pc * stage_lines);
-        load_lines(maps, ring_w + (uint32_t)pstage * stage_bytes,
-                   p_base + (p_first + pk * nw) * p_lines + (int64_t)pc * stage_lines, lh,
-                   bar_w + 8u * (uint32_t)pstage);
+        const int lh = min(stage_lines, p_left);
+        tma_stage(maps, ring_w + (uint32_t)pstage * stage_bytes, p_cur, lh, stage_lines,
+                  bar_w + 8u * (uint32_t)pstage);
         if (++pstage == stages) pstage = 0;
         ++issued;
-        if (++pc == p_nc) {
-            pc = 0;
-            if (++pk == p_rows) next_job();
+        p_cur += lh;
+        if ((p_left -= lh) == 0) {
+            if (--p_rows == 0) {
+                next_job();
+            } else {
+                p_row += p_step;
+                p_cur = p_row;
+                p_left = p_lines;
+            }
         }
     };
     if (lane == 0) {
@@ -919,13 +925,160 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     }
 }
 
+// Interleaved schedule: the plain search's row order applied to each job in
+// turn.  Warp w of the grid (G warps) takes rows w, w + G, w + 2G, ... of job
+// 0, then of job 1, and so on, so at any time the whole GPU streams one compact
+// window of consecutive rows, as the plain search does; the producer lane runs
+// ahead across job boundaries.  The CTA synchronises at every job (to swap the
+// weights), and skips jobs in which none of its warps has a row.
+template <int U>
+__global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
+    k_bscreen_il(const __grid_constant__ BatchMaps maps, const JobDesc *__restrict__ jobs,
+                 BatchMeta *meta, int max_words, int stages, int stage_lines) {
+    extern __shared__ __align__(16) float sv[];
+    __shared__ float s_min[32];
+    const int nw = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t stage_bytes = (uint32_t)stage_lines * kLineBytes;
+    const uint32_t sv32 = smem_u32(sv);
+    const uint32_t ring0 = (uint32_t)align_up(sv32 + (uint32_t)max_words * 4u, 1024);
+    const uint32_t bars0 = ring0 + (uint32_t)nw * stages * stage_bytes;
+    const uint32_t ring_w = ring0 + (uint32_t)warp * stages * stage_bytes;
+    const uint32_t bar_w = bars0 + (uint32_t)(warp * stages * 8);
+    if (lane == 0) {
+        for (int s = 0; s < stages; ++s) mbar_init(bar_w + 8 * s, 1);
+        fence_barrier_init();
+    }
+    const int nj = meta->njobs;
+    const int64_t gw = (int64_t)blockIdx.x * nw + warp;
+    const int64_t G = (int64_t)gridDim.x * nw;
+    auto rows_of = [&](const JobDesc &J) -> int64_t {
+        return (J.rs->in_round && gw < J.nfeat) ? (J.nfeat - 1 - gw) / G + 1 : 0;
+    };
+    // producer (lane 0): job of the next load, the arena line of its stage, the
+    // lines left in its row and the rows left in the job
+    int pj = -1, pstage = 0, p_lines = 0, p_left = 0;
+    int64_t p_row = 0, p_cur = 0, p_step = 0, p_rows = 0, issued = 0;
+    auto next_job = [&]() {
+        for (++pj; pj < nj; ++pj) {
+            const JobDesc &J = jobs[pj];
+            p_rows = rows_of(J);
+            if (p_rows) {
+                p_lines = J.lines;
+                p_left = p_lines;
+                p_row = J.line_base + gw * p_lines;
+                p_cur = p_row;
+                p_step = G * p_lines;
+                return;
+            }
+        }
+    };
+    auto issue_next = [&]() {
+        if (pj >= nj) return;
+        const int lh = min(stage_lines, p_left);
+        tma_stage(maps, ring_w + (uint32_t)pstage * stage_bytes, (int32_t)p_cur, lh, stage_lines,
+                  bar_w + 8u * (uint32_t)pstage);
+        if (++pstage == stages) pstage = 0;
+        ++issued;
+        p_cur += lh;
+        if ((p_left -= lh) == 0) {
+            if (--p_rows == 0) {
+                next_job();
+            } else {
+                p_row += p_step;
+                p_cur = p_row;
+                p_left = p_lines;
+            }
+        }
+    };
+    if (lane == 0) {
+        next_job();
+        for (int s = 0; s < stages; ++s) issue_next();
+    }
+    __syncwarp();
+    int cstage = 0, prev = -1;
+    uint32_t cpar = 0;
+    int64_t consumed = 0;
+    bool ok = true;  // false once one of this warp's waits timed out
+    for (int j = 0; j < nj; ++j) {
+        const JobDesc &J = jobs[j];
+        if (!J.rs->in_round || (int64_t)blockIdx.x * nw >= J.nfeat) continue;  // uniform over the CTA
+        __syncthreads();  // every warp is done with the previous job's weights and minima
+        if (prev >= 0 && threadIdx.x == 0) {
+            float m = INFINITY;
+            for (int w = 0; w < nw; ++w) m = fminf(m, s_min[w]);
+            if (m < INFINITY) atomicMin(&jobs[prev].rs->screen_min_bits, __float_as_uint(fmaxf(m, 0.f)));
+        }
+        for (int i = threadIdx.x; i < J.lay.words; i += blockDim.x) sv[i] = J.v[i];
+        __syncthreads();
+        prev = j;
+        const int lines = J.lines;
+        const int nc = (lines + stage_lines - 1) / stage_lines;
+        const int64_t nrows = ok ? rows_of(J) : 0;
+        const float Tp = (float)J.rs->t_pos, Tm = (float)J.rs->t_neg;
+        float *ferr = J.ferr;
+        float wmin = INFINITY;
+        for (int64_t k = 0; k < nrows && ok; ++k) {
+            const int64_t f = gw + k * G;
+            float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
+            for (int c = 0; c < nc; ++c) {
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
+                    ok = false;
+                    break;
+                }
+                const int lh = min(stage_lines, lines - c * stage_lines);
+                scan_stage<U>(ring_w + (uint32_t)cstage * stage_bytes, lh >> 2, lane, sv, ahi, alo, bmx, bmn);
+                __syncwarp();
+                if (lane == 0) {
+                    fence_proxy_async_smem();
+                    issue_next();
+                }
+                if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
+                ++consumed;
+            }
+            if (!ok) break;
+            const float e = finish_row(ahi, alo, bmx, bmn, Tp, Tm, lane);
+            if (lane == 0) ferr[f] = e;
+            wmin = fminf(wmin, e);
+        }
+        if (!ok && lane == 0) {
+            atomicOr(&meta->flags, kFlagWaitTimeout);
+            atomicOr(&J.rs->flags, kFlagWaitTimeout);
+        }
+        if (lane == 0) s_min[warp] = wmin;
+    }
+    __syncthreads();
+    if (prev >= 0 && threadIdx.x == 0) {
+        float m = INFINITY;
+        for (int w = 0; w < nw; ++w) m = fminf(m, s_min[w]);
+        if (m < INFINITY) atomicMin(&jobs[prev].rs->screen_min_bits, __float_as_uint(fmaxf(m, 0.f)));
+    }
+    if (!ok && lane == 0) {
+        // wait (bounded) for this warp's copies still in flight before the CTA exits
+        const int64_t pending = issued - consumed;
+        for (int64_t s = 0; s < pending; ++s) {
+            mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar, 100000000ull);
+            if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
+        }
+    }
+}
+
 cudaError_t launch_bscreen(const BatchMaps &maps, const JobDesc *jobs, const WorkItem *items,
-                           BatchMeta *meta, int max_words, const SearchShape &shape, bool partitioned,
+                           BatchMeta *meta, int max_words, const SearchShape &shape, int schedule,
                            int grid, cudaStream_t st) {
     const size_t sm = bscreen_smem_bytes(shape, max_words);
     const int threads = shape.warps * 32;
     const int sl = shape.box_lines;
-    if (partitioned) {
+    if (schedule == VJB_BATCH_INTERLEAVED) {
+        switch (shape.unroll) {
+        case 1: k_bscreen_il<1><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages, sl); break;
+        case 3: k_bscreen_il<3><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages, sl); break;
+        case 4: k_bscreen_il<4><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages, sl); break;
+        default: k_bscreen_il<2><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages, sl);
+        }
+        return cudaGetLastError();
+    }
+    if (schedule == VJB_BATCH_PARTITIONED) {
         switch (shape.unroll) {
         case 1: k_bscreen_pt<1><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages, sl); break;
         case 3: k_bscreen_pt<3><<<grid, threads, sm, st>>>(maps, jobs, meta, max_words, shape.stages, sl); break;
@@ -956,6 +1109,10 @@ cudaError_t set_bscreen_smem_limit(int bytes) {
     set((const void *)k_bscreen_pt<2>);
     set((const void *)k_bscreen_pt<3>);
     set((const void *)k_bscreen_pt<4>);
+    set((const void *)k_bscreen_il<1>);
+    set((const void *)k_bscreen_il<2>);
+    set((const void *)k_bscreen_il<3>);
+    set((const void *)k_bscreen_il<4>);
     return e;
 }
 

@@ -1021,7 +1021,7 @@ struct vjb_batch {
     int items_cap = 0;
     bool dirty = true;  // the device job table must be rebuilt
     SearchShape shape{16, 2, 1, 3, 24};
-    int rows_per_warp = VJB_BATCH_PARTITIONED;  // > 0: work queue of that many rows per warp and item
+    int rows_per_warp = VJB_BATCH_INTERLEAVED;  // the schedule; > 0: work queue of that many rows per warp
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     int64_t launches = 0;
@@ -1052,10 +1052,12 @@ int batch_encode_maps(vjb_batch *b) {
             return fail(VJB_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
         encode = reinterpret_cast<EncodeTiledFn>(fn);
     }
-    for (int k = 0; k < 4; ++k) {
+    const int S = b->shape.box_lines;  // stage height of the batched search
+    memset(&b->maps, 0, sizeof b->maps);
+    for (int k = 0; k < S / 4; ++k) {
         cuuint64_t dims[2] = {(cuuint64_t)kLineElems, (cuuint64_t)b->arena_lines};
         cuuint64_t strides[1] = {(cuuint64_t)kLineBytes};
-        cuuint32_t box[2] = {(cuuint32_t)kLineElems, (cuuint32_t)(kBoxLinesMax >> k)};
+        cuuint32_t box[2] = {(cuuint32_t)kLineElems, (cuuint32_t)(k == 0 ? S : 4 * k)};
         cuuint32_t estr[2] = {1, 1};
         CUresult r = encode(&b->maps.m[k], CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, b->arena, dims, strides, box,
                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1153,7 +1155,7 @@ int batch_enqueue_round(vjb_batch *b, const EventTriple *ev) {
     if (ev) CK(cudaEventRecordWithFlags((*ev)[0], b->stream, cudaEventRecordExternal));
     CK(launch_bbegin(b->d_jobs, b->d_meta, b->stream));
     CK(launch_bscreen(b->maps, b->d_jobs, b->d_items, b->d_meta, kBatchMaxWords, b->shape,
-                      b->rows_per_warp <= 0, g * b->shape.ctas_per_sm, b->stream));
+                      b->rows_per_warp, g * b->shape.ctas_per_sm, b->stream));
     if (ev) CK(cudaEventRecordWithFlags((*ev)[1], b->stream, cudaEventRecordExternal));
     CK(launch_bshortlist(b->d_jobs, b->d_meta, g * 4, b->stream));
     CK(launch_brescan(b->d_jobs, b->d_meta, g * 2, b->stream));
@@ -1345,7 +1347,8 @@ int vjb_batch_create(vjb_batch **out, int device, void *cuda_stream, int64_t tab
             return bail(fail(VJB_ECUDA, "stream creation failed"));
         b->own_stream = true;
     }
-    b->arena_lines = table_budget_bytes / kLineBytes;
+    // the search addresses arena lines with 32-bit coordinates
+    b->arena_lines = std::min<int64_t>(table_budget_bytes / kLineBytes, INT32_MAX);
     cudaError_t e = cudaMalloc(&b->arena, (size_t)b->arena_lines * kLineBytes);
     if (e != cudaSuccess) return bail(fail(VJB_ENOMEM, "table arena of %lld bytes: %s", (long long)table_budget_bytes, cudaGetErrorString(e)));
     if (cudaMalloc(&b->d_jobs, sizeof(JobDesc) * kMaxBatchJobs) != cudaSuccess ||
@@ -1488,10 +1491,11 @@ int vjb_batch_autotune(vjb_batch *b, int32_t trial_rounds, int32_t *rounds_run, 
     CK(cudaSetDevice(b->device));
     // (warps, stages, unroll, features per warp and work item); results do not
     // depend on the shape, so every trial round is a real round of the jobs
-    // (rows VJB_BATCH_PARTITIONED: the partitioned schedule, else the work queue)
-    constexpr int IL = VJB_BATCH_PARTITIONED;
-    static const int kTries[][5] = {{16, 2, 3, 24, IL}, {12, 2, 4, 32, IL}, {16, 2, 3, 24, 16}, {16, 2, 3, 24, 32},
-                                    {12, 2, 4, 32, 32}, {8, 3, 4, 32, IL},  {16, 2, 2, 16, IL}, {8, 2, 3, 24, IL}};
+    // (rows: VJB_BATCH_INTERLEAVED / VJB_BATCH_PARTITIONED schedules, else the work queue)
+    constexpr int IL = VJB_BATCH_INTERLEAVED;
+    constexpr int PT = VJB_BATCH_PARTITIONED;
+    static const int kTries[][5] = {{16, 2, 3, 24, IL}, {16, 2, 3, 24, PT}, {16, 2, 3, 24, 16}, {16, 2, 3, 24, 32},
+                                    {12, 2, 4, 32, IL}, {12, 2, 4, 32, PT}, {12, 2, 4, 32, 32}, {16, 2, 3, 24, 64}};
     const SearchShape keep = b->shape;
     const int keep_rpw = b->rows_per_warp;
     double best = -1.0;
@@ -1508,6 +1512,8 @@ int vjb_batch_autotune(vjb_batch *b, int32_t trial_rounds, int32_t *rounds_run, 
         b->rows_per_warp = t[4];
         b->dirty = true;
         b->drop_graph();
+        rc = batch_encode_maps(b);
+        if (rc) return rc;
         float ms = 0.f;
         rc = batch_run(b, 1, nullptr);  // first round of a shape: graph set-up, not timed
         if (rc == VJB_OK) rc = batch_run(b, trial_rounds, &ms);
@@ -1526,6 +1532,8 @@ int vjb_batch_autotune(vjb_batch *b, int32_t trial_rounds, int32_t *rounds_run, 
     b->rows_per_warp = best_rpw;
     b->dirty = true;
     b->drop_graph();
+    const int rce = batch_encode_maps(b);
+    if (rce) return rce;
     if (rounds_run) *rounds_run = ran;
     if (n_trials) *n_trials = std::min(ntr, std::max(max_trials, 0));
     return VJB_OK;
@@ -1579,14 +1587,14 @@ int vjb_batch_set_search_shape(vjb_batch *b, const vjb_search_shape *in, int32_t
         if (in->ctas_per_sm) s.ctas_per_sm = in->ctas_per_sm;
         if (in->box_lines) s.box_lines = in->box_lines;
     }
-    if (!batch_shape_ok(b, s) || rows_per_warp < VJB_BATCH_PARTITIONED || rows_per_warp > 4096)
+    if (!batch_shape_ok(b, s) || rows_per_warp < VJB_BATCH_INTERLEAVED || rows_per_warp > 4096)
         return fail(VJB_EINVAL, "batch search shape (%d warps, %d stages, unroll %d, %d rows per warp) not usable",
                     s.warps, s.stages, s.unroll, rows_per_warp);
     b->shape = s;
     if (rows_per_warp) b->rows_per_warp = rows_per_warp;
     b->dirty = true;
     b->drop_graph();
-    return VJB_OK;
+    return batch_encode_maps(b);
 }
 
 int vjb_batch_get_info(vjb_batch *b, vjb_batch_info *out) {

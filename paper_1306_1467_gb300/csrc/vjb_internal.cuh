@@ -206,12 +206,16 @@ cudaError_t launch_rescan(const JobDesc &J, int grid, cudaStream_t st);
 cudaError_t launch_update_a(const JobDesc &J, cudaStream_t st);
 cudaError_t launch_update_b(const JobDesc &J, cudaStream_t st);
 // batched rounds over the jobs of a device job table
+// The table arena as [lines][64 entries]: m[0] loads a whole stage of the
+// batched search (its box is the stage height S); m[k], 0 < k < S / 4, loads
+// 4k lines (the tail of a row).  One copy per stage either way.
+constexpr int kBatchMaps = kBoxLinesMax / 4;
 struct BatchMaps {
-    CUtensorMap m[4];  // the table arena as [lines][64 entries]; boxes of 32, 16, 8 and 4 lines
+    CUtensorMap m[kBatchMaps];
 };
 cudaError_t launch_bbegin(JobDesc *jobs, BatchMeta *meta, cudaStream_t st);
 cudaError_t launch_bscreen(const BatchMaps &maps, const JobDesc *jobs, const WorkItem *items,
-                           BatchMeta *meta, int max_words, const SearchShape &shape, bool partitioned,
+                           BatchMeta *meta, int max_words, const SearchShape &shape, int schedule,
                            int grid, cudaStream_t st);
 cudaError_t launch_bshortlist(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st);
 cudaError_t launch_brescan(const JobDesc *jobs, BatchMeta *meta, int grid, cudaStream_t st);

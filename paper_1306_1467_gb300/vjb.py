@@ -22,7 +22,7 @@ OK, DONE_PERFECT, DONE_NOGAIN = 0, 1, 2
 EINVAL, ESTATE, ENOMEM, ECUDA, EDEVICE, EFULL = -1, -2, -3, -4, -5, -6
 MAX_SAMPLES = 32766
 REQ_QUEUED, REQ_PREPARING, REQ_TRAINING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3, 4
-BATCH_PARTITIONED = -1
+BATCH_PARTITIONED, BATCH_INTERLEAVED = -1, -2
 HAAR_TYPES = ("3H", "3V", "2H", "2V", "4")
 
 
@@ -495,7 +495,7 @@ class Batch:
     def set_search_shape(self, warps: int = 0, stages: int = 0, unroll: int = 0, rows_per_warp: int = 0,
                          box_lines: int = 0):
         """Batched search launch shape; rows_per_warp > 0 selects the work queue with that many
-        features per warp and item, BATCH_PARTITIONED the partitioned schedule, 0 keeps a field."""
+        features per warp and item, BATCH_INTERLEAVED / BATCH_PARTITIONED the other schedules, 0 keeps a field."""
         sh = SearchShapeC(int(warps), int(stages), 0, int(unroll), int(box_lines))
         self._check(self._lib.vjb_batch_set_search_shape(self._h, C.byref(sh), int(rows_per_warp)))
 

@@ -106,7 +106,7 @@ def test_batch_jobs_change_between_calls():
         b.remove_job(a)
         c = b.add_job(*jc, rounds=5)
         assert b.train(2) == 2
-        assert b.info()["rows_per_warp"] == vjb.BATCH_PARTITIONED
+        assert b.info()["rows_per_warp"] == vjb.BATCH_INTERLEAVED
         b.set_search_shape(warps=8, stages=3, rows_per_warp=4)  # work queue; results do not depend on it
         b.train()
         _same(b, bb, *jb, 10)
@@ -151,3 +151,21 @@ def test_batch_autotune_keeps_results():
         b.train()
         _same(b, a, *ja, 30)
         _same(b, c, *jb, 30)
+
+
+def test_batch_schedules_agree():
+    """The interleaved, partitioned and work-queue schedules, switched between
+    rounds, give every job its plain result."""
+    from paper_1306_1467_gb300 import vjb
+    jobs = [synth.make_windows(700, 1200, 12, 12, seed=81), synth.make_windows(3000, 5200, 10, 10, seed=82),
+            synth.make_windows(90, 150, 14, 14, seed=83)]
+    budget = sum(vjb.Batch.table_bytes(px.shape[0], px.shape[1], px.shape[2]) for px, _ in jobs)
+    with vjb.Batch(budget) as b:
+        ids = [b.add_job(px, y, rounds=9) for px, y in jobs]
+        for sched, warps, unroll, box in ((vjb.BATCH_INTERLEAVED, 16, 3, 24), (vjb.BATCH_PARTITIONED, 12, 4, 32),
+                                          (8, 16, 2, 16)):
+            b.set_search_shape(warps=warps, unroll=unroll, rows_per_warp=sched, box_lines=box)
+            assert b.info()["rows_per_warp"] == sched and b.info()["box_lines"] == box
+            b.train(3)
+        for jid, (px, y) in zip(ids, jobs):
+            _same(b, jid, px, y, 9)
