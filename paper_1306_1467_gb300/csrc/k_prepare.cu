@@ -434,13 +434,18 @@ __global__ void __launch_bounds__(kPkThreads, 2)
     const int pos0 = wp * 32 * IPT + lane;
     const DevFeature d = feat[f0 + blockIdx.x];
 
-    // the feature on every window (K2's arithmetic)
+    // the feature on every window (K2's arithmetic), four windows per thread
+    // and corner load
     int32_t lo = INT_MAX, hi = INT_MIN;
-    for (int p = threadIdx.x; p < n; p += kPkThreads) {
-        const int32_t x = haar_value(ii_t, ii_stride, w, d.type, d.x, d.y, d.w, d.h, p);
-        skey[p] = static_cast<uint32_t>(x);
-        lo = min(lo, x);
-        hi = max(hi, x);
+    for (int q = threadIdx.x; 4 * q < n; q += kPkThreads) {
+        const int p = 4 * q;
+        const int4 x = haar_value4(ii_t, ii_stride, w, d.type, d.x, d.y, d.w, d.h, p);
+        reinterpret_cast<uint4 *>(skey)[q] = make_uint4((uint32_t)x.x, (uint32_t)x.y, (uint32_t)x.z, (uint32_t)x.w);
+        lo = min(lo, x.x);
+        hi = max(hi, x.x);
+        if (p + 1 < n) { lo = min(lo, x.y); hi = max(hi, x.y); }
+        if (p + 2 < n) { lo = min(lo, x.z); hi = max(hi, x.z); }
+        if (p + 3 < n) { lo = min(lo, x.w); hi = max(hi, x.w); }
     }
 #pragma unroll
     for (int s = 16; s; s >>= 1) {
@@ -550,22 +555,22 @@ __global__ void __launch_bounds__(kPkThreads, 2)
     const int run = npad / 32;
     if (L.dual) {
         // bank-balanced copy choice per gather group (see k_sort_rows); the
-        // loads of the 32 banks live in registers as bit planes: bank b holds
-        // l1:b + l2:b + l3:b entries (a load above 3 counts as 3)
+        // loads of the 32 banks live in registers as 2-bit counters, banks
+        // 0-15 in cl and 16-31 in ch (a load above 3 counts as 3)
         for (int g = threadIdx.x; g < run; g += kPkThreads) {
-            uint32_t l1 = 0, l2 = 0, l3 = 0, mask = 0;
-            auto level = [&](int b) { return ((l1 >> b) & 1u) + ((l2 >> b) & 1u) + ((l3 >> b) & 1u); };
+            uint32_t cl = 0, ch = 0, mask = 0;
+            auto level = [&](int b) { return ((b < 16 ? cl : ch) >> (2 * (b & 15))) & 3u; };
             auto inc = [&](int b) {
-                const uint32_t bit = 1u << b;
-                if (!(l1 & bit)) l1 |= bit;
-                else if (!(l2 & bit)) l2 |= bit;
-                else l3 |= bit;
+                if (level(b) == 3u) return;
+                const uint32_t one = 1u << (2 * (b & 15));
+                if (b < 16) cl += one;
+                else ch += one;
             };
             auto dec = [&](int b) {
-                const uint32_t bit = 1u << b;
-                if (l3 & bit) l3 &= ~bit;
-                else if (l2 & bit) l2 &= ~bit;
-                else l1 &= ~bit;
+                if (level(b) == 0u) return;
+                const uint32_t one = 1u << (2 * (b & 15));
+                if (b < 16) cl -= one;
+                else ch -= one;
             };
             bool pad_seen = false;
             for (int k = 0; k < 32; ++k) {

@@ -216,7 +216,9 @@ int apply_shape(vjb_ctx *c) {
         c->bmin_cap = c->screen_grid;
     }
     c->shortlist_grid = c->num_sms * 2;
-    c->rescan_grid = c->num_sms * 2;
+    // a round shortlists a handful of features: a few CTAs (each takes every
+    // grid-th candidate) launch and hand over to the last one faster than two per SM
+    c->rescan_grid = 16;
     c->shape_set = true;
     c->drop_graph();
     return VJB_OK;
@@ -1158,7 +1160,7 @@ int batch_enqueue_round(vjb_batch *b, const EventTriple *ev) {
                       b->rows_per_warp, g * b->shape.ctas_per_sm, b->stream));
     if (ev) CK(cudaEventRecordWithFlags((*ev)[1], b->stream, cudaEventRecordExternal));
     CK(launch_bshortlist(b->d_jobs, b->d_meta, g * 4, b->stream));
-    CK(launch_brescan(b->d_jobs, b->d_meta, g * 2, b->stream));
+    CK(launch_brescan(b->d_jobs, b->d_meta, std::min(g, 128), b->stream));
     CK(launch_bupdate_a(b->d_jobs, b->d_meta, g * 4, b->stream));
     CK(launch_bupdate_b(b->d_jobs, b->d_meta, g * 4, b->stream));
     if (ev) CK(cudaEventRecordWithFlags((*ev)[2], b->stream, cudaEventRecordExternal));
