@@ -313,9 +313,9 @@ __global__ void __launch_bounds__(kSortThreads, 1)
                     int word = sidx[p];
                     const int k = (P >> 3) & 31, g = (P >> 8) * kChunkElems + (P & 7);  // p = k * run + g
                     if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
-                    e = static_cast<uint16_t>(word | (step ? kFlagBit : 0));
+                    e = make_entry(word, step, P);
                 } else {
-                    e = static_cast<uint16_t>(n);
+                    e = make_entry(n, false, P);
                 }
                 out[P] = e;
             }
@@ -327,9 +327,9 @@ __global__ void __launch_bounds__(kSortThreads, 1)
         uint16_t e;
         if (p < n) {
             const bool step = (p == n - 1) || (skey[p] < skey[p + 1]);
-            e = static_cast<uint16_t>(sidx[p] | (step ? kFlagBit : 0));
+            e = make_entry(sidx[p], step, P);
         } else {
-            e = static_cast<uint16_t>(n);
+            e = make_entry(n, false, P);
         }
         out[P] = e;
     }
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kSortThreads, 1)
 
 // Validation of a finished table: every entry before position n names a word
 // inside the weight array other than the padding word, every entry from n on
-// is the padding word n.  Sets kFlagBadTable in `flags` otherwise.  The search
+// is the padding entry (word n, no flag).  Sets kFlagBadTable in `flags` otherwise.  The search
 // kernels rely on this to gather weights without bounds checks.  One CTA per
 // row at a time, one 16-byte chunk (8 entries) per thread.
 __global__ void k_check_rows(const uint16_t *__restrict__ rows, int64_t nfeat, WeightLayout L,
@@ -354,15 +354,15 @@ __global__ void k_check_rows(const uint16_t *__restrict__ rows, int64_t nfeat, W
             if (p0 + kChunkElems <= n) {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const uint32_t a = wd[j] & kIndexMask, b = (wd[j] >> 16) & kIndexMask;
+                    const uint32_t a = wd[j] & kIndexMask, b = wd[j] >> 17;
                     bad |= a >= words || a == pad || b >= words || b == pad;
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
-                    const uint32_t word = e & kIndexMask;
-                    bad |= (p0 + j < n) ? (word >= words || word == pad) : (e != pad);
+                    const uint32_t word = (uint32_t)entry_word(e, j);
+                    bad |= (p0 + j < n) ? (word >= words || word == pad) : (e != make_entry(n, false, j));
                 }
             }
         }
@@ -614,9 +614,9 @@ __global__ void __launch_bounds__(kPkThreads, 2)
                 const int k = (P >> 3) & 31, g = (P >> 8) * kChunkElems + (P & 7);
                 if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
             }
-            e = static_cast<uint16_t>(word | (step ? kFlagBit : 0));
+            e = make_entry(word, step, P);
         } else {
-            e = static_cast<uint16_t>(n);
+            e = make_entry(n, false, P);
         }
         out[P] = e;
     }

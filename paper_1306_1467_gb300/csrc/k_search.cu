@@ -109,8 +109,8 @@ __device__ __forceinline__ void scan_pieces(uint32_t sbase, int t0, int lane, co
     for (int u = 0; u < U; ++u)
 #pragma unroll
         for (int j = 0; j < E / 2; ++j) {
-            g[u][2 * j] = sv[wd[u][j] & kIndexMask];
-            g[u][2 * j + 1] = sv[(wd[u][j] >> 16) & kIndexMask];
+            g[u][2 * j] = sv[wd[u][j] & kIndexMask];  // even position: word | flag << 15
+            g[u][2 * j + 1] = sv[wd[u][j] >> 17];      // odd position: (word << 1 | flag) << 16
         }
     float a[U], mx[U], mn[U];
 #pragma unroll
@@ -124,7 +124,7 @@ __device__ __forceinline__ void scan_pieces(uint32_t sbase, int t0, int lane, co
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             a[u] += g[u][j];
-            const uint32_t fl = (j & 1) ? (wd[u][j >> 1] & 0x80000000u) : (wd[u][j >> 1] & 0x8000u);
+            const uint32_t fl = (j & 1) ? (wd[u][j >> 1] & 0x10000u) : (wd[u][j >> 1] & 0x8000u);
             minmax_if(fl, a[u], mx[u], mn[u]);
         }
 #pragma unroll
@@ -417,8 +417,8 @@ __device__ RunResult rescan_run(const uint16_t *__restrict__ row, int run, int k
 #pragma unroll
             for (int j = 0; j < kChunkElems; ++j) {
                 const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
-                a = df_add_f(a, __ldg(v + (e & kIndexMask)));
-                if (e & kFlagBit) {
+                a = df_add_f(a, __ldg(v + entry_word(e, j)));
+                if (entry_flag(e, j)) {
                     const int pos = k * run + t * kChunkElems + j + 1;
                     if (df_less(lmx, a)) { lmx = a; lsx = pos; }
                     if (df_less(a, lmn)) { lmn = a; lsn = pos; }

@@ -146,7 +146,8 @@ __device__ void update_a_block(const JobDesc &J, int blk) {
         bool h;
         if (!forced) {
             // sorted position k: the first s positions are "below" the threshold
-            i = word_to_sample(J.rows[(size_t)f * J.npad + phys_of(k, J.npad / 32)] & kIndexMask, J.lay);
+            const int P = phys_of(k, J.npad / 32);
+            i = word_to_sample(entry_word(J.rows[(size_t)f * J.npad + P], P), J.lay);
             const bool bl = k < s;
             h = (p > 0) ? bl : !bl;
         } else {
@@ -209,7 +210,8 @@ __device__ void update_a_finish(const JobDesc &J, double M, double T, double B) 
         // p=-1 -> value at position s-1 (min-1 at s = 0)
         const uint16_t *row = J.rows + (size_t)f * J.npad;
         auto val_at = [&](int pos) {
-            const int i = word_to_sample(row[phys_of(pos, J.npad / 32)] & kIndexMask, J.lay);
+            const int P = phys_of(pos, J.npad / 32);
+            const int i = word_to_sample(entry_word(row[P], P), J.lay);
             return haar_value(J.ii, J.ii_stride, J.win_w, d.type, d.x, d.y, d.w, d.h, i);
         };
         if (p > 0) theta = (s < n) ? val_at(s) : val_at(n - 1) + 1;

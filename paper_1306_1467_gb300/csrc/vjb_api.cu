@@ -888,8 +888,10 @@ int vjb_sorted_rows(vjb_ctx *c, int64_t f0, int64_t nf, uint16_t *out) {
     const int run = c->npad / 32;
     for (int64_t r = 0; r < nf; ++r)
         for (int e = 0; e < c->n; ++e) {
-            const uint16_t x = raw[(size_t)r * c->npad + phys_of(e, run)];
-            out[(size_t)r * c->n + e] = (uint16_t)((x & kFlagBit) | word_to_sample(x & kIndexMask, c->lay));
+            const int P = phys_of(e, run);
+            const uint16_t x = raw[(size_t)r * c->npad + P];
+            out[(size_t)r * c->n + e] =
+                (uint16_t)((entry_flag(x, P) ? kFlagBit : 0) | word_to_sample(entry_word(x, P), c->lay));
         }
     return VJB_OK;
 }

@@ -105,6 +105,19 @@ __host__ __device__ __forceinline__ int logical_of(int phys, int run) {
 }
 constexpr uint16_t kFlagBit = 0x8000u;
 constexpr uint16_t kIndexMask = 0x7FFFu;
+// Table entries are 15-bit weight-word offsets with a split flag, packed by
+// physical position: an entry at an even position is word | flag << 15, one at
+// an odd position (the high half of a 32-bit word) word << 1 | flag, so that a
+// 32-bit pair gives its high word with one shift.  Padding: word n, no flag.
+__host__ __device__ __forceinline__ uint16_t make_entry(int word, bool flag, int phys) {
+    return (phys & 1) ? (uint16_t)((word << 1) | (flag ? 1 : 0)) : (uint16_t)(word | (flag ? kFlagBit : 0));
+}
+__host__ __device__ __forceinline__ int entry_word(uint32_t e, int phys) {
+    return (phys & 1) ? (int)((e & 0xffffu) >> 1) : (int)(e & kIndexMask);
+}
+__host__ __device__ __forceinline__ bool entry_flag(uint32_t e, int phys) {
+    return (phys & 1) ? (e & 1u) != 0 : (e & kFlagBit) != 0;
+}
 
 // Margin (in units of 2^-24 times the weight total) within which a feature's
 // FP32 screened error must lie of the smallest one to be re-scanned
