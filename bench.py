@@ -218,6 +218,26 @@ def run_reference(a, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def replica_seed(seed: int, rank: int) -> int:
+    """Seed of rank `rank`'s job: replicas train independent jobs."""
+    return seed + 1000 * rank
+
+
+def slowest_rank_ms(times_ms, dist, device):
+    """Element-wise max over ranks of a list of timed-region durations (ms)."""
+    if dist is None:
+        return [float(t) for t in times_ms]
+    import torch
+    t = torch.tensor([float(x) for x in times_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def whole_job_rate(world: int, steps: int, rounds: int, ms: float) -> float:
+    """Rounds of every rank's jobs per second of the slowest rank's timed region."""
+    return world * steps * rounds / (ms / 1000.0)
+
+
 def run_ours(a, ws, rank, local):
     import numpy as np
     import torch
@@ -232,7 +252,7 @@ def run_ours(a, ws, rank, local):
     dev = torch.device("cuda", local)
     cfg = dict(synth.WORKLOADS[a.workload])
     rounds = cfg.pop("rounds")
-    cfg["seed"] = cfg["seed"] + 1000 * rank  # replicas train independent jobs
+    cfg["seed"] = replica_seed(cfg["seed"], rank)
     px, y = synth.make_windows(**cfg)
     n, H, W = px.shape
     stream = torch.cuda.Stream(device=dev)
@@ -319,16 +339,11 @@ def run_ours(a, ws, rank, local):
                "d2h_bytes_per_step": int(rounds * STUMP_BYTES), "ms_per_step": e2e_ms / a.steps,
                "_ms": e2e_ms}
 
-    if dist:
-        t = torch.tensor([ms, e2e["_ms"] if e2e else 0.0], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
-        if e2e:
-            e2e["_ms"] = float(t[1])
-    total_rounds = ws * a.steps * rounds
-    value = total_rounds / (ms / 1000.0)
+    ms, e2e_ms = slowest_rank_ms([ms, e2e["_ms"] if e2e else 0.0], dist, dev)
+    value = whole_job_rate(ws, a.steps, rounds, ms)
     if e2e:
-        e2e["value"] = total_rounds / (e2e.pop("_ms") / 1000.0)
+        e2e.pop("_ms")
+        e2e["value"] = whole_job_rate(ws, a.steps, rounds, e2e_ms)
 
     search_bytes = 2.0 * nf * n
     avg_search_ms = tm["search_ms_total"] / max(tm["rounds"], 1)
