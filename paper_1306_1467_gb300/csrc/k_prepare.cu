@@ -258,69 +258,78 @@ __global__ void __launch_bounds__(kSortThreads, 1)
     __syncthreads();
     uint16_t *out = rows + (size_t)blockIdx.x * npad;
     const int run = npad / 32;  // entries per lane run (see phys_of)
-    if constexpr (IPT <= 16) {
-        if (L.dual) {
-            // With two weight copies, choose per entry which copy the search
-            // gathers from.  One gather instruction of the search kernel reads
-            // entry r of every lane run: the 32 entries k * run + r, k = 0..31.
-            // For each such group, greedily put each entry in the less loaded
-            // of its two banks (copy A: i mod 32, copy B: rot(i) mod 32), then
-            // let entries move to a lighter bank.  Bank loads are kept per
-            // thread, bank-major so that the threads do not share banks.
-            uint32_t *gchoice = hist + kRadix * kSortWarps;  // one mask per group
-            uint8_t *ld = reinterpret_cast<uint8_t *>(hist) + threadIdx.x;
-            for (int g = threadIdx.x; g < run; g += kSortThreads) {
+    if (L.dual) {
+        // With two weight copies, choose per entry which copy the search
+        // gathers from.  One gather instruction of the search kernel reads
+        // entry r of every lane run: the 32 entries k * run + r, k = 0..31.
+        // For each such group, greedily put each entry that has a copy B
+        // (samples below L.nb) in the less loaded of its two banks (copy A:
+        // i mod 32, copy B: rot(i) mod 32), then let such entries move to a
+        // lighter bank.  Bank loads are kept per thread, bank-major so that
+        // the threads do not share banks.  The split flags first go into bit 15
+        // of the sample indices (n <= 32767), which frees the keys' space for
+        // the choices of the 32-item variant.
+        for (int p = threadIdx.x; p < n; p += kSortThreads)
+            if (p == n - 1 || skey[p] < skey[p + 1]) sidx[p] |= 0x8000u;
+        __syncthreads();
+        uint32_t *gchoice = IPT <= 16 ? hist + kRadix * kSortWarps : skey;  // one mask per group
+        uint8_t *ld = reinterpret_cast<uint8_t *>(hist) + threadIdx.x;
+        for (int g = threadIdx.x; g < run; g += kSortThreads) {
 #pragma unroll
-                for (int b = 0; b < 32; ++b) ld[b * kSortThreads] = 0;
-                uint32_t mask = 0;
-                bool pad_seen = false;
+            for (int b = 0; b < 32; ++b) ld[b * kSortThreads] = 0;
+            uint32_t mask = 0;
+            bool pad_seen = false;
+            for (int k = 0; k < 32; ++k) {
+                const int p = k * run + g;
+                if (p >= n) {
+                    if (!pad_seen) ld[(n & 31) * kSortThreads]++;  // padding: one broadcast read
+                    pad_seen = true;
+                    continue;
+                }
+                const int i = sidx[p] & 0x7fff;
+                const int ba = i & 31, bb = rot_b(i) & 31;
+                if (i < L.nb && ld[bb * kSortThreads] < ld[ba * kSortThreads]) {
+                    ld[bb * kSortThreads]++;
+                    mask |= 1u << k;
+                } else {
+                    ld[ba * kSortThreads]++;
+                }
+            }
+            // two passes of single moves: an entry leaves its bank when the
+            // other one is at least two entries lighter
+            for (int pass = 0; pass < 2; ++pass)
                 for (int k = 0; k < 32; ++k) {
                     const int p = k * run + g;
-                    if (p >= n) {
-                        if (!pad_seen) ld[(n & 31) * kSortThreads]++;  // padding: one broadcast read
-                        pad_seen = true;
-                        continue;
-                    }
-                    const int i = sidx[p];
+                    if (p >= n) break;
+                    const int i = sidx[p] & 0x7fff;
+                    if (i >= L.nb) continue;
                     const int ba = i & 31, bb = rot_b(i) & 31;
-                    if (ld[bb * kSortThreads] < ld[ba * kSortThreads]) { ld[bb * kSortThreads]++; mask |= 1u << k; }
-                    else ld[ba * kSortThreads]++;
-                }
-                // two passes of single moves: an entry leaves its bank when the
-                // other one is at least two entries lighter
-                for (int pass = 0; pass < 2; ++pass)
-                    for (int k = 0; k < 32; ++k) {
-                        const int p = k * run + g;
-                        if (p >= n) break;
-                        const int i = sidx[p];
-                        const int ba = i & 31, bb = rot_b(i) & 31;
-                        const bool onb = (mask >> k) & 1u;
-                        const int cur = onb ? bb : ba, oth = onb ? ba : bb;
-                        if (ld[cur * kSortThreads] > ld[oth * kSortThreads] + 1) {
-                            ld[cur * kSortThreads]--;
-                            ld[oth * kSortThreads]++;
-                            mask ^= 1u << k;
-                        }
+                    const bool onb = (mask >> k) & 1u;
+                    const int cur = onb ? bb : ba, oth = onb ? ba : bb;
+                    if (ld[cur * kSortThreads] > ld[oth * kSortThreads] + 1) {
+                        ld[cur * kSortThreads]--;
+                        ld[oth * kSortThreads]++;
+                        mask ^= 1u << k;
                     }
-                gchoice[g] = mask;
-            }
-            __syncthreads();
-            for (int P = threadIdx.x; P < npad; P += kSortThreads) {
-                const int p = logical_of(P, run);
-                uint16_t e;
-                if (p < n) {
-                    const bool step = (p == n - 1) || (skey[p] < skey[p + 1]);
-                    int word = sidx[p];
-                    const int k = (P >> 3) & 31, g = (P >> 8) * kChunkElems + (P & 7);  // p = k * run + g
-                    if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
-                    e = make_entry(word, step, P);
-                } else {
-                    e = make_entry(n, false, P);
                 }
-                out[P] = e;
-            }
-            return;
+            gchoice[g] = mask;
         }
+        __syncthreads();
+        for (int P = threadIdx.x; P < npad; P += kSortThreads) {
+            const int p = logical_of(P, run);
+            uint16_t e;
+            if (p < n) {
+                const uint32_t x = sidx[p];
+                int word = (int)(x & 0x7fffu);
+                const int k = (P >> 3) & 31, g = (P >> 8) * kChunkElems + (P & 7);  // p = k * run + g
+                if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
+                e = make_entry(word, (x & 0x8000u) != 0, P);
+            } else {
+                e = make_entry(n, false, P);
+            }
+            out[P] = e;
+        }
+        return;
     }
     for (int P = threadIdx.x; P < npad; P += kSortThreads) {
         const int p = logical_of(P, run);
@@ -582,7 +591,7 @@ __global__ void __launch_bounds__(kPkThreads, 2)
                 }
                 const int i = (int)(skey[p] & imask);
                 const int ba = i & 31, bb = rot_b(i) & 31;
-                if (level(bb) < level(ba)) { inc(bb); mask |= 1u << k; }
+                if (i < L.nb && level(bb) < level(ba)) { inc(bb); mask |= 1u << k; }
                 else inc(ba);
             }
             for (int pass = 0; pass < kPkRefinePasses; ++pass)
@@ -590,6 +599,7 @@ __global__ void __launch_bounds__(kPkThreads, 2)
                     const int p = k * run + g;
                     if (p >= n) break;
                     const int i = (int)(skey[p] & imask);
+                    if (i >= L.nb) continue;
                     const int ba = i & 31, bb = rot_b(i) & 31;
                     const bool onb = (mask >> k) & 1u;
                     const int cur = onb ? bb : ba, oth = onb ? ba : bb;
@@ -645,8 +655,6 @@ cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, c
                              int32_t *flags, cudaStream_t st) {
     if (nf <= 0) return cudaSuccess;
     const int n = L.n;
-    // two weight copies need the bank-choice space, which the 32-item variant lacks
-    if (L.dual && n > kSortThreads * 16) return cudaErrorInvalidValue;
     // packed items: 14-bit sample index, value span below 2^18
     if (n <= kPkThreads * 32 && 255LL * w * h < (1LL << 18)) {
 #define VJB_PK_CASE(I) launch_sort_packed<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, flags, st)

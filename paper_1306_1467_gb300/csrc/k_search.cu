@@ -64,11 +64,13 @@ WeightLayout make_layout(int n, bool allow_dual) {
     WeightLayout L;
     L.n = n;
     const int off_b = (int)align_up((size_t)n + 1, 32);
-    const int words_dual = off_b + (int)align_up((size_t)n, 32);
-    // table entries hold 15-bit word offsets
-    L.dual = (allow_dual && words_dual <= 32768) ? 1 : 0;
+    // table entries hold 15-bit word offsets: copy B takes what is left of the
+    // 32,768 words after copy A, whole 32-sample blocks (all n while n <= 16,351)
+    const int room = off_b < 32768 ? (32768 - off_b) / 32 * 32 : 0;
+    L.nb = allow_dual ? (n < room ? n : room) : 0;
+    L.dual = L.nb > 0 ? 1 : 0;
     L.off_b = L.dual ? off_b : 0;
-    L.words = L.dual ? words_dual : (int)align_up((size_t)n + 1, 4);
+    L.words = L.dual ? off_b + (int)align_up((size_t)L.nb, 32) : (int)align_up((size_t)n + 1, 4);
     return L;
 }
 

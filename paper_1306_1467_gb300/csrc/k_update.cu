@@ -37,7 +37,7 @@ __device__ __forceinline__ double cta_sum(double x, double *red) {
 
 __device__ __forceinline__ void store_v(float *v, const WeightLayout &L, int i, float x) {
     v[i] = x;
-    if (L.dual) v[L.off_b + rot_b(i)] = x;
+    if (L.dual && i < L.nb) v[L.off_b + rot_b(i)] = x;
 }
 
 __global__ void __launch_bounds__(kOneCta)

@@ -24,9 +24,10 @@ struct DevFeature {
 // entry that balances the banks.  Word n holds 0 and is the padding entry.
 struct WeightLayout {
     int n;
-    int dual;    // 1: two copies, 0: copy A only
+    int dual;    // 1: a copy B exists, 0: copy A only
     int off_b;   // first word of copy B (a multiple of 32), 0 without it
     int words;   // array length in floats
+    int nb;      // samples 0 .. nb-1 have a copy B (nb = n unless 15-bit offsets run out)
 };
 
 __host__ __device__ __forceinline__ int rot_b(int i) {

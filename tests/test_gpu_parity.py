@@ -383,3 +383,27 @@ def test_strong_classifier_matches_oracle(tiny_prepared):
         assert np.array_equal(lab_inf, h0.astype(np.uint8))
         with pytest.raises(vjb.VJBError):
             tr.classify(px, [dict(stumps[0], feature=10 ** 7)])
+
+
+@pytest.mark.parametrize("n_pos,n_neg", [(6000, 12000), (3000, 13383), (9000, 23000)])
+def test_large_n_partial_second_copy(n_pos, n_neg):
+    """N above 16,351: the second weight copy covers only the samples that fit
+    15-bit word offsets (none at N close to 32,767).  Sorted rows bit-exact,
+    screened errors within the screening bound, same-input parity of rounds."""
+    from paper_1306_1467_gb300 import vjb
+    px, y = synth.make_windows(n_pos, n_neg, 8, 8, seed=n_pos + n_neg)
+    P = O.Prepared(px, y)
+    with _trainer() as tr:
+        feats = tr.prepare(px, y)
+        assert np.array_equal(feats, P.desc)
+        _check_rows(tr.sorted_rows(0, feats.shape[0]), P.vals, P.order)
+        n = n_pos + n_neg
+        assert tr.info()["dual_weights"] == (1 if n < 32735 else 0)
+        stumps = _round_parity(tr, P.vals, P.order, y, 3, vjb)
+        assert len(stumps) == 3
+        w32 = tr.get_weights()
+        wn = O.normalize(w32.astype(np.float64))
+        best = O.feature_best_sorted(P.vals, P.order, y, wn)
+        tr.train_round()
+        scr = tr.screen_errors().astype(np.float64)
+        assert np.max(np.abs(scr - best["err"])) <= SCREEN_TOL
