@@ -140,7 +140,8 @@ template <int IPT>
 __global__ void __launch_bounds__(kSortThreads, 1)
     k_sort_rows(const int32_t *__restrict__ ii_t, int ii_stride, int w,
                 const DevFeature *__restrict__ feat, int64_t f0, WeightLayout L,
-                uint16_t *__restrict__ rows, int npad) {
+                uint16_t *__restrict__ rows, int npad, const int32_t *__restrict__ row_list) {
+    const int row = row_list ? row_list[blockIdx.x] : (int)blockIdx.x;  // row of the tile
     constexpr int NP = kSortThreads * IPT;
     const int n = L.n;
     extern __shared__ __align__(16) uint8_t smem[];
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kSortThreads, 1)
 
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int pos0 = wp * 32 * IPT + lane;
-    const DevFeature d = feat[f0 + blockIdx.x];
+    const DevFeature d = feat[f0 + row];
 
     // the feature on every window, into shared memory (K2's arithmetic)
     int32_t lo = INT_MAX, hi = INT_MIN;
@@ -256,7 +257,7 @@ __global__ void __launch_bounds__(kSortThreads, 1)
         sidx[p] = static_cast<uint16_t>((j & 1) ? (ipk[j >> 1] >> 16) : (ipk[j >> 1] & 0xffffu));
     }
     __syncthreads();
-    uint16_t *out = rows + (size_t)blockIdx.x * npad;
+    uint16_t *out = rows + (size_t)row * npad;
     const int run = npad / 32;  // entries per lane run (see phys_of)
     if (L.dual) {
         // With two weight copies, choose per entry which copy the search
@@ -395,12 +396,13 @@ static size_t sort_smem() {
 template <int IPT>
 static cudaError_t launch_sort_ipt(const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
                                    int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows,
-                                   int npad, cudaStream_t st) {
+                                   int npad, const int32_t *row_list, cudaStream_t st) {
     const size_t sm = sort_smem<IPT>();
     cudaError_t e = cudaFuncSetAttribute(k_sort_rows<IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
-    k_sort_rows<IPT><<<(unsigned)nf, kSortThreads, sm, st>>>(ii_t, ii_stride, w, feat, f0, L, rows, npad);
+    k_sort_rows<IPT><<<(unsigned)nf, kSortThreads, sm, st>>>(ii_t, ii_stride, w, feat, f0, L, rows, npad,
+                                                            row_list);
     return cudaGetLastError();
 }
 
@@ -425,19 +427,21 @@ constexpr int kPkHistStride = kPkWarps + 1;
 constexpr int kPkHistWords = kPkRadix * kPkHistStride;
 static_assert(kPkThreads * 32 / 4 <= kPkHistWords, "histogram space too small for bank loads");
 
-template <int IPT>
-__global__ void __launch_bounds__(kPkThreads, 2)
+template <int IPT, int TH>
+__global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
     k_sort_rows_packed(const int32_t *__restrict__ ii_t, int ii_stride, int w,
                        const DevFeature *__restrict__ feat, int64_t f0, WeightLayout L,
-                       uint16_t *__restrict__ rows, int npad, int32_t *flags) {
-    constexpr int NP = kPkThreads * IPT;
+                       uint16_t *__restrict__ rows, int npad, int32_t *ovf) {
+    constexpr int NP = TH * IPT;
+    constexpr int WARPS = TH / 32, HSTRIDE = WARPS + 1, HWORDS = kPkRadix * HSTRIDE;
+    constexpr int GROUPS = NP / 32;  // lane-run groups of the longest row
     const int n = L.n;
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t *skey = reinterpret_cast<uint32_t *>(smem);            // NP items
-    uint32_t *hist = skey + NP;                                     // kPkHistWords
-    uint32_t *gchoice = hist + kPkHistWords;                        // kMaxGroups
-    uint32_t *ws = gchoice + kMaxGroups;                            // kPkWarps
-    int32_t *mm = reinterpret_cast<int32_t *>(ws + kPkWarps);       // 2
+    uint32_t *hist = skey + NP;                                     // HWORDS
+    uint32_t *gchoice = hist + HWORDS;                              // GROUPS
+    uint32_t *ws = gchoice + GROUPS;                                // WARPS
+    int32_t *mm = reinterpret_cast<int32_t *>(ws + WARPS);       // 2
 
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int pos0 = wp * 32 * IPT + lane;
@@ -446,7 +450,7 @@ __global__ void __launch_bounds__(kPkThreads, 2)
     // the feature on every window (K2's arithmetic), four windows per thread
     // and corner load
     int32_t lo = INT_MAX, hi = INT_MIN;
-    for (int q = threadIdx.x; 4 * q < n; q += kPkThreads) {
+    for (int q = threadIdx.x; 4 * q < n; q += TH) {
         const int p = 4 * q;
         const int4 x = haar_value4(ii_t, ii_stride, w, d.type, d.x, d.y, d.w, d.h, p);
         reinterpret_cast<uint4 *>(skey)[q] = make_uint4((uint32_t)x.x, (uint32_t)x.y, (uint32_t)x.z, (uint32_t)x.w);
@@ -471,8 +475,8 @@ __global__ void __launch_bounds__(kPkThreads, 2)
     const int bits = span ? 32 - __clz(span) : 0;
     const int ib = 32 - __clz((uint32_t)(n - 1));  // bits of a sample index
     const uint32_t imask = (1u << ib) - 1u;
-    if (bits + ib > 32) {  // the host's size check rules this out; never pack silently wrong
-        if (threadIdx.x == 0) atomicOr(flags, kFlagBadTable);
+    if (bits + ib > 32) {  // value and index do not fit one word: the two-word sort takes the row
+        if (threadIdx.x == 0) ovf[1 + atomicAdd(ovf, 1)] = (int32_t)blockIdx.x;
         return;
     }
     uint32_t c[IPT];
@@ -487,7 +491,7 @@ __global__ void __launch_bounds__(kPkThreads, 2)
     const uint32_t lt = lanemask_lt();
     for (int shift = 0; shift < bits; shift += kPkDigitBits) {
         const int sh = ib + shift;
-        for (int k = threadIdx.x; k < kPkHistWords; k += kPkThreads) hist[k] = 0;
+        for (int k = threadIdx.x; k < HWORDS; k += TH) hist[k] = 0;
         __syncthreads();
         // each item's rank among the warp's earlier items of its digit, in
         // position order (item j before item j + 1, lanes in order), two per word
@@ -499,8 +503,8 @@ __global__ void __launch_bounds__(kPkThreads, 2)
             const int leader = __ffs(peers) - 1;
             uint32_t old = 0;
             if (lane == leader) {
-                old = hist[dg * kPkHistStride + wp];
-                hist[dg * kPkHistStride + wp] = old + __popc(peers);
+                old = hist[dg * HSTRIDE + wp];
+                hist[dg * HSTRIDE + wp] = old + __popc(peers);
             }
             old = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
             if (j & 1) rk[j >> 1] |= old << 16;
@@ -508,13 +512,13 @@ __global__ void __launch_bounds__(kPkThreads, 2)
         }
         __syncthreads();
         {
-            constexpr int PER = kPkRadix * kPkWarps / kPkThreads;  // 16
+            constexpr int PER = kPkRadix * WARPS / TH;  // 16
             uint32_t cnt[PER];
             uint32_t s = 0;
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
                 const int lin = threadIdx.x * PER + q;
-                cnt[q] = hist[(lin / kPkWarps) * kPkHistStride + (lin % kPkWarps)];
+                cnt[q] = hist[(lin / WARPS) * HSTRIDE + (lin % WARPS)];
                 s += cnt[q];
             }
             // CTA-wide exclusive scan of the per-thread sums
@@ -527,21 +531,21 @@ __global__ void __launch_bounds__(kPkThreads, 2)
             if (lane == 31) ws[wp] = inc;
             __syncthreads();
             if (wp == 0) {
-                const uint32_t t = lane < kPkWarps ? ws[lane] : 0u;
+                const uint32_t t = lane < WARPS ? ws[lane] : 0u;
                 uint32_t ti = t;
 #pragma unroll
                 for (int dd = 1; dd < 32; dd <<= 1) {
                     const uint32_t y = __shfl_up_sync(0xffffffffu, ti, dd);
                     if (lane >= dd) ti += y;
                 }
-                if (lane < kPkWarps) ws[lane] = ti - t;
+                if (lane < WARPS) ws[lane] = ti - t;
             }
             __syncthreads();
             uint32_t off = ws[wp] + inc - s;
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
                 const int lin = threadIdx.x * PER + q;
-                hist[(lin / kPkWarps) * kPkHistStride + (lin % kPkWarps)] = off;
+                hist[(lin / WARPS) * HSTRIDE + (lin % WARPS)] = off;
                 off += cnt[q];
             }
         }
@@ -549,7 +553,7 @@ __global__ void __launch_bounds__(kPkThreads, 2)
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const uint32_t dg = (c[j] >> sh) & (kPkRadix - 1);
-            skey[hist[dg * kPkHistStride + wp] + ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = c[j];
+            skey[hist[dg * HSTRIDE + wp] + ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = c[j];
         }
         __syncthreads();
 #pragma unroll
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(kPkThreads, 2)
         // bank-balanced copy choice per gather group (see k_sort_rows); the
         // loads of the 32 banks live in registers as 2-bit counters, banks
         // 0-15 in cl and 16-31 in ch (a load above 3 counts as 3)
-        for (int g = threadIdx.x; g < run; g += kPkThreads) {
+        for (int g = threadIdx.x; g < run; g += TH) {
             uint32_t cl = 0, ch = 0, mask = 0;
             auto level = [&](int b) { return ((b < 16 ? cl : ch) >> (2 * (b & 15))) & 3u; };
             auto inc = [&](int b) {
@@ -613,7 +617,7 @@ __global__ void __launch_bounds__(kPkThreads, 2)
         }
         __syncthreads();
     }
-    for (int P = threadIdx.x; P < npad; P += kPkThreads) {
+    for (int P = threadIdx.x; P < npad; P += TH) {
         const int p = logical_of(P, run);
         uint16_t e;
         if (p < n) {
@@ -632,45 +636,29 @@ __global__ void __launch_bounds__(kPkThreads, 2)
     }
 }
 
-template <int IPT>
+template <int IPT, int TH>
 static size_t sort_packed_smem() {
-    return (size_t)kPkThreads * IPT * 4 + (size_t)(kPkHistWords + kMaxGroups + kPkWarps + 2) * 4;
+    return (size_t)TH * IPT * 4 + (size_t)(kPkRadix * (TH / 32 + 1) + TH * IPT / 32 + TH / 32 + 2) * 4;
 }
 
-template <int IPT>
+template <int IPT, int TH = kPkThreads>
 static cudaError_t launch_sort_packed(const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
                                       int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows,
-                                      int npad, int32_t *flags, cudaStream_t st) {
-    const size_t sm = sort_packed_smem<IPT>();
-    cudaError_t e = cudaFuncSetAttribute(k_sort_rows_packed<IPT>,
+                                      int npad, int32_t *ovf, cudaStream_t st) {
+    const size_t sm = sort_packed_smem<IPT, TH>();
+    cudaError_t e = cudaFuncSetAttribute(k_sort_rows_packed<IPT, TH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_sort_rows_packed<IPT><<<(unsigned)nf, kPkThreads, sm, st>>>(ii_t, ii_stride, w, feat, f0, L, rows, npad,
-                                                                   flags);
+    k_sort_rows_packed<IPT, TH><<<(unsigned)nf, TH, sm, st>>>(ii_t, ii_stride, w, feat, f0, L, rows, npad, ovf);
     return cudaGetLastError();
 }
 
-cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, const DevFeature *feat,
-                             int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows, int npad,
-                             int32_t *flags, cudaStream_t st) {
-    if (nf <= 0) return cudaSuccess;
+// Two-word sort of `nf` rows of the tile (all of them, or those listed).
+static cudaError_t launch_sort_wide(const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
+                                   int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows, int npad,
+                                   const int32_t *row_list, cudaStream_t st) {
     const int n = L.n;
-    // packed items: 14-bit sample index, value span below 2^18
-    if (n <= kPkThreads * 32 && 255LL * w * h < (1LL << 18)) {
-#define VJB_PK_CASE(I) launch_sort_packed<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, flags, st)
-        const int ipt = (n + kPkThreads - 1) / kPkThreads;
-        if (ipt <= 4) return VJB_PK_CASE(4);
-        if (ipt <= 8) return VJB_PK_CASE(8);
-        if (ipt <= 12) return VJB_PK_CASE(12);
-        if (ipt <= 16) return VJB_PK_CASE(16);
-        if (ipt <= 20) return VJB_PK_CASE(20);
-        if (ipt <= 24) return VJB_PK_CASE(24);
-        if (ipt <= 28) return VJB_PK_CASE(28);
-        if (ipt <= 30) return VJB_PK_CASE(30);
-        return VJB_PK_CASE(32);
-#undef VJB_PK_CASE
-    }
-#define VJB_SORT_CASE(I) launch_sort_ipt<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, st)
+#define VJB_SORT_CASE(I) launch_sort_ipt<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, row_list, st)
     if (n <= kSortThreads * 1) return VJB_SORT_CASE(1);
     if (n <= kSortThreads * 2) return VJB_SORT_CASE(2);
     if (n <= kSortThreads * 4) return VJB_SORT_CASE(4);
@@ -678,6 +666,49 @@ cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, c
     if (n <= kSortThreads * 16) return VJB_SORT_CASE(16);
     return VJB_SORT_CASE(32);
 #undef VJB_SORT_CASE
+}
+
+// Rows of a tile: the packed sort for every row (512 threads up to 16,384
+// samples, 1024 above), then the two-word sort for the rows whose value span
+// and sample index do not fit one word, which the packed sort lists in ovf
+// (count, then rows; 1 + nf ints of device memory).  Waits for the stream
+// when it reads the count.
+cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, const DevFeature *feat,
+                             int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows, int npad,
+                             int32_t *ovf, cudaStream_t st) {
+    (void)h;
+    if (nf <= 0) return cudaSuccess;
+    const int n = L.n;
+    cudaError_t e = cudaMemsetAsync(ovf, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    if (n <= kPkThreads * 32) {
+#define VJB_PK_CASE(I) launch_sort_packed<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, ovf, st)
+        const int ipt = (n + kPkThreads - 1) / kPkThreads;
+        if (ipt <= 4) e = VJB_PK_CASE(4);
+        else if (ipt <= 8) e = VJB_PK_CASE(8);
+        else if (ipt <= 12) e = VJB_PK_CASE(12);
+        else if (ipt <= 16) e = VJB_PK_CASE(16);
+        else if (ipt <= 20) e = VJB_PK_CASE(20);
+        else if (ipt <= 24) e = VJB_PK_CASE(24);
+        else if (ipt <= 28) e = VJB_PK_CASE(28);
+        else if (ipt <= 30) e = VJB_PK_CASE(30);
+        else e = VJB_PK_CASE(32);
+#undef VJB_PK_CASE
+    } else {
+#define VJB_PK_WIDE(I) launch_sort_packed<I, 1024>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, ovf, st)
+        const int ipt = (n + 1023) / 1024;
+        if (ipt <= 20) e = VJB_PK_WIDE(20);
+        else if (ipt <= 24) e = VJB_PK_WIDE(24);
+        else if (ipt <= 28) e = VJB_PK_WIDE(28);
+        else e = VJB_PK_WIDE(32);
+#undef VJB_PK_WIDE
+    }
+    if (e != cudaSuccess) return e;
+    int32_t count = 0;
+    e = cudaMemcpyAsync(&count, ovf, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess || count == 0) return e;
+    return launch_sort_wide(ii_t, ii_stride, w, feat, f0, count, L, rows, npad, ovf + 1, st);
 }
 
 }  // namespace vjb

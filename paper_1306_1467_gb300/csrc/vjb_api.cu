@@ -499,13 +499,20 @@ int prepare_tables(vjb_ctx *c) {
     }
     // feature values (the K2 arithmetic, fused into the sort) and sort, a tile of rows per launch
     const int64_t tile = std::max<int64_t>(1, std::min<int64_t>(c->nfeat, 65535));
+    int32_t *d_ovf = nullptr;  // rows the packed sort hands to the two-word sort
+    CK(cudaMalloc(&d_ovf, sizeof(int32_t) * (size_t)(1 + tile)));
     for (int64_t f0 = 0; f0 < c->nfeat; f0 += tile) {
         const int64_t nf = std::min(tile, c->nfeat - f0);
-        CK(launch_sort_rows(c->d_ii, c->ii_stride, c->w, c->h, c->d_feat, f0, nf, c->lay,
-                            c->d_rows + (size_t)f0 * c->npad, c->npad, flags_ptr(c), c->stream));
+        const cudaError_t e = launch_sort_rows(c->d_ii, c->ii_stride, c->w, c->h, c->d_feat, f0, nf, c->lay,
+                                               c->d_rows + (size_t)f0 * c->npad, c->npad, d_ovf, c->stream);
+        if (e != cudaSuccess) {
+            cudaFree(d_ovf);
+            return fail(VJB_ECUDA, "sort of rows %lld..: %s", (long long)f0, cudaGetErrorString(e));
+        }
         c->launches += 1;
     }
     CK(cudaStreamSynchronize(c->stream));
+    dfree(d_ovf);
     // the search kernels gather through the table without bounds checks: validate it once
     CK(launch_check_rows(c->d_rows, c->nfeat, c->lay, c->npad, flags_ptr(c), c->num_sms * 8, c->stream));
     c->launches += 1;

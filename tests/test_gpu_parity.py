@@ -407,3 +407,34 @@ def test_large_n_partial_second_copy(n_pos, n_neg):
         tr.train_round()
         scr = tr.screen_errors().astype(np.float64)
         assert np.max(np.abs(scr - best["err"])) <= SCREEN_TOL
+
+
+def test_rows_too_wide_for_one_word_take_the_two_word_sort():
+    """At N > 16,384 a packed item has 15 index bits, so a row whose value
+    span needs more than 17 bits cannot be packed; the two-word sort takes it.
+    Windows half black / half white (and the inverse) give the full-window
+    two-rectangle features a span of 146,880.  Those rows and a few ordinary
+    ones are compared with the oracle's stable order bit for bit."""
+    from paper_1306_1467_gb300 import vjb
+    rng = np.random.Generator(np.random.PCG64(5))
+    n = 17000
+    px = rng.integers(100, 156, size=(n, 24, 24), dtype=np.uint8)
+    half = rng.random(n) < 0.5
+    px[half, :, :12] = 0
+    px[half, :, 12:] = 255
+    px[~half, :, :12] = 255
+    px[~half, :, 12:] = 0
+    y = (rng.random(n) < 0.4).astype(np.uint8)
+    desc, _ = O.haar_enumerate(24, 24)
+    wide = [int(np.flatnonzero((desc[:, 0] == t) & (desc[:, 1] == 0) & (desc[:, 2] == 0) &
+                               (desc[:, 3] == 24) & (desc[:, 4] == 24))[0]) for t in (vjb.HAAR_TYPES.index("2H"),)]
+    picks = wide + [0, 1000, 50000, desc.shape[0] - 1]
+    vals = O.feature_values(px, desc[picks])
+    span = vals.max(axis=1).astype(np.int64) - vals.min(axis=1)
+    assert span[0] >= 1 << 17  # does not fit one word with a 15-bit index
+    order = O.sort_rows(vals)
+    with _trainer() as tr:
+        feats = tr.prepare(px, y)
+        assert np.array_equal(feats, desc)
+        for k, f in enumerate(picks):
+            _check_rows(tr.sorted_rows(f, 1), vals[k:k + 1], order[k:k + 1])
