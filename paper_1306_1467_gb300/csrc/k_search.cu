@@ -655,7 +655,7 @@ __device__ __forceinline__ void tma_stage(const BatchMaps &maps, uint32_t dst, i
 }
 
 template <int U>
-__global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
+__global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
     k_bscreen(const __grid_constant__ BatchMaps maps, const JobDesc *__restrict__ jobs,
               const WorkItem *__restrict__ items, BatchMeta *meta, int max_words, int stages, int stage_lines) {
     extern __shared__ __align__(16) float sv[];
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
 // The CTA synchronises only when it moves to the next job (to swap the weights
 // in shared memory), which with ranges this long happens once or twice a round.
 template <int U>
-__global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
+__global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
     k_bscreen_pt(const __grid_constant__ BatchMaps maps, const JobDesc *__restrict__ jobs,
                  BatchMeta *meta, int max_words, int stages, int stage_lines) {
     extern __shared__ __align__(16) float sv[];
@@ -810,14 +810,13 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
         b = min(g1 - J.feat_base, J.nfeat);
         if (!J.rs->in_round || a >= b) a = b = 0;
     };
-    auto rows_of = [&](int64_t a, int64_t b) -> int64_t {
-        return b - a > warp ? (b - a - warp + nw - 1) / nw : 0;
+    auto rows_of = [&](int64_t a, int64_t b) -> int {
+        return b - a > warp ? (int)((b - a - warp + nw - 1) / nw) : 0;
     };
     // producer (lane 0): job of the next load, the arena line of its stage, the
     // lines left in its row and the rows left in the job, in this warp's order
-    int pj = j0 - 1, pstage = 0, p_lines = 0, p_left = 0;
+    int pj = j0 - 1, pstage = 0, p_lines = 0, p_left = 0, p_rows = 0, issued = 0;
     int32_t p_row = 0, p_cur = 0, p_step = 0;
-    int64_t p_rows = 0, issued = 0;
     auto next_job = [&]() {
         for (++pj; pj < nj && jobs[pj].feat_base < g1; ++pj) {
             const JobDesc &J = jobs[pj];
@@ -860,7 +859,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     __syncwarp();
     int cstage = 0, prev = -1;
     uint32_t cpar = 0;
-    int64_t consumed = 0;
+    int consumed = 0;
     bool ok = true;  // false once one of this warp's waits timed out
     for (int j = j0; j < nj && jobs[j].feat_base < g1; ++j) {
         const JobDesc &J = jobs[j];
@@ -878,12 +877,13 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
         prev = j;
         const int lines = J.lines;
         const int nc = (lines + stage_lines - 1) / stage_lines;
-        const int64_t nrows = ok ? rows_of(a, b) : 0;
+        const int nrows = ok ? rows_of(a, b) : 0;
         const float Tp = (float)J.rs->t_pos, Tm = (float)J.rs->t_neg;
         float *ferr = J.ferr;
         float wmin = INFINITY;
-        for (int64_t k = 0; k < nrows && ok; ++k) {
-            const int64_t f = a + warp + k * nw;
+        const int f0 = (int)a + warp;
+        for (int k = 0; k < nrows && ok; ++k) {
+            const int f = f0 + k * nw;
             float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
             for (int c = 0; c < nc; ++c) {
                 if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
@@ -919,8 +919,8 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     }
     if (!ok && lane == 0) {
         // wait (bounded) for this warp's copies still in flight before the CTA exits
-        const int64_t pending = issued - consumed;
-        for (int64_t s = 0; s < pending; ++s) {
+        const int pending = issued - consumed;
+        for (int s = 0; s < pending; ++s) {
             mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar, 100000000ull);
             if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
         }
@@ -934,7 +934,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
 // ahead across job boundaries.  The CTA synchronises at every job (to swap the
 // weights), and skips jobs in which none of its warps has a row.
 template <int U>
-__global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
+__global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
     k_bscreen_il(const __grid_constant__ BatchMaps maps, const JobDesc *__restrict__ jobs,
                  BatchMeta *meta, int max_words, int stages, int stage_lines) {
     extern __shared__ __align__(16) float sv[];
@@ -952,15 +952,17 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
         fence_barrier_init();
     }
     const int nj = meta->njobs;
-    const int64_t gw = (int64_t)blockIdx.x * nw + warp;
-    const int64_t G = (int64_t)gridDim.x * nw;
-    auto rows_of = [&](const JobDesc &J) -> int64_t {
-        return (J.rs->in_round && gw < J.nfeat) ? (J.nfeat - 1 - gw) / G + 1 : 0;
+    // 32-bit state: rows, lines of the arena and counts fit, and the scan
+    // below needs the registers
+    const int gw = blockIdx.x * nw + warp;
+    const int G = gridDim.x * nw;
+    auto rows_of = [&](const JobDesc &J) -> int {
+        return (J.rs->in_round && gw < J.nfeat) ? (int)((J.nfeat - 1 - gw) / G + 1) : 0;
     };
     // producer (lane 0): job of the next load, the arena line of its stage, the
     // lines left in its row and the rows left in the job
-    int pj = -1, pstage = 0, p_lines = 0, p_left = 0;
-    int64_t p_row = 0, p_cur = 0, p_step = 0, p_rows = 0, issued = 0;
+    int pj = -1, pstage = 0, p_lines = 0, p_left = 0, p_rows = 0, issued = 0;
+    int32_t p_row = 0, p_cur = 0, p_step = 0;
     auto next_job = [&]() {
         for (++pj; pj < nj; ++pj) {
             const JobDesc &J = jobs[pj];
@@ -968,7 +970,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
             if (p_rows) {
                 p_lines = J.lines;
                 p_left = p_lines;
-                p_row = J.line_base + gw * p_lines;
+                p_row = (int32_t)(J.line_base + (int64_t)gw * p_lines);
                 p_cur = p_row;
                 p_step = G * p_lines;
                 return;
@@ -978,7 +980,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     auto issue_next = [&]() {
         if (pj >= nj) return;
         const int lh = min(stage_lines, p_left);
-        tma_stage(maps, ring_w + (uint32_t)pstage * stage_bytes, (int32_t)p_cur, lh, stage_lines,
+        tma_stage(maps, ring_w + (uint32_t)pstage * stage_bytes, p_cur, lh, stage_lines,
                   bar_w + 8u * (uint32_t)pstage);
         if (++pstage == stages) pstage = 0;
         ++issued;
@@ -1000,7 +1002,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     __syncwarp();
     int cstage = 0, prev = -1;
     uint32_t cpar = 0;
-    int64_t consumed = 0;
+    int consumed = 0;
     bool ok = true;  // false once one of this warp's waits timed out
     for (int j = 0; j < nj; ++j) {
         const JobDesc &J = jobs[j];
@@ -1016,12 +1018,12 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
         prev = j;
         const int lines = J.lines;
         const int nc = (lines + stage_lines - 1) / stage_lines;
-        const int64_t nrows = ok ? rows_of(J) : 0;
+        const int nrows = ok ? rows_of(J) : 0;
         const float Tp = (float)J.rs->t_pos, Tm = (float)J.rs->t_neg;
         float *ferr = J.ferr;
         float wmin = INFINITY;
-        for (int64_t k = 0; k < nrows && ok; ++k) {
-            const int64_t f = gw + k * G;
+        for (int k = 0; k < nrows && ok; ++k) {
+            const int f = gw + k * G;
             float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
             for (int c = 0; c < nc; ++c) {
                 if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
@@ -1057,8 +1059,8 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : 640, 1)
     }
     if (!ok && lane == 0) {
         // wait (bounded) for this warp's copies still in flight before the CTA exits
-        const int64_t pending = issued - consumed;
-        for (int64_t s = 0; s < pending; ++s) {
+        const int pending = issued - consumed;
+        for (int s = 0; s < pending; ++s) {
             mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar, 100000000ull);
             if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
         }
