@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libvjb.so")
-SOURCES = ["vjb_api.cu", "k_prepare.cu", "k_search.cu", "k_update.cu", "k_classify.cu"]
+SOURCES = ["vjb_api.cu", "vjb_batch.cu", "k_prepare.cu", "k_search.cu", "k_update.cu", "k_classify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -40,7 +40,8 @@ def _flags(ptxas_verbose: bool) -> list[str]:
 
 def _newest_input() -> float:
     files = [os.path.join(CSRC, s) for s in SOURCES]
-    files += glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    files += glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
+    files += glob.glob(os.path.join(INCLUDE, "*.h"))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(p) for p in files)
 
