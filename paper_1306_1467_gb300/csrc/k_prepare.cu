@@ -4,6 +4,8 @@
 // feature in value order).
 #include <limits.h>
 
+#include <type_traits>
+
 #include "vjb_device.cuh"
 #include "vjb_internal.cuh"
 
@@ -427,6 +429,8 @@ constexpr int kPkHistStride = kPkWarps + 1;
 constexpr int kPkHistWords = kPkRadix * kPkHistStride;
 static_assert(kPkThreads * 32 / 4 <= kPkHistWords, "histogram space too small for bank loads");
 
+__host__ __device__ constexpr bool packed_ranks_in_smem(int ipt, int th) { return th <= 512 && ipt >= 20 && ipt <= 30; }
+
 template <int IPT, int TH>
 __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
     k_sort_rows_packed(const int32_t *__restrict__ ii_t, int ii_stride, int w,
@@ -435,13 +439,21 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
     constexpr int NP = TH * IPT;
     constexpr int WARPS = TH / 32, HSTRIDE = WARPS + 1, HWORDS = kPkRadix * HSTRIDE;
     constexpr int GROUPS = NP / 32;  // lane-run groups of the longest row
+    // 512-thread CTAs of 20 to 30 items keep the items' ranks in shared memory
+    // (registers would spill) and count in 16 bits (counts and offsets stay
+    // below 2^16) so that two CTAs still fit an SM; the others keep them in
+    // registers
+    constexpr bool RS = packed_ranks_in_smem(IPT, TH);
+    using HT = typename std::conditional<RS, uint16_t, uint32_t>::type;
     const int n = L.n;
     extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t *skey = reinterpret_cast<uint32_t *>(smem);            // NP items
-    uint32_t *hist = skey + NP;                                     // HWORDS
-    uint32_t *gchoice = hist + HWORDS;                              // GROUPS
-    uint32_t *ws = gchoice + GROUPS;                                // WARPS
-    int32_t *mm = reinterpret_cast<int32_t *>(ws + WARPS);       // 2
+    uint32_t *skey = reinterpret_cast<uint32_t *>(smem);                        // NP items
+    uint16_t *rks = reinterpret_cast<uint16_t *>(skey + NP);                   // NP ranks (RS)
+    HT *hist = reinterpret_cast<HT *>(RS ? (uint8_t *)(rks + NP) : (uint8_t *)(skey + NP));  // HWORDS
+    uint32_t *gchoice = reinterpret_cast<uint32_t *>(
+        reinterpret_cast<uint8_t *>(hist) + (((size_t)HWORDS * sizeof(HT) + 15) & ~(size_t)15));  // GROUPS
+    uint32_t *ws = gchoice + GROUPS;                                            // WARPS
+    int32_t *mm = reinterpret_cast<int32_t *>(ws + WARPS);                      // 2
 
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     const int pos0 = wp * 32 * IPT + lane;
@@ -494,8 +506,9 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
         for (int k = threadIdx.x; k < HWORDS; k += TH) hist[k] = 0;
         __syncthreads();
         // each item's rank among the warp's earlier items of its digit, in
-        // position order (item j before item j + 1, lanes in order), two per word
-        uint32_t rk[(IPT + 1) / 2];
+        // position order (item j before item j + 1, lanes in order): in shared
+        // memory at the item's position (RS), else two per register
+        uint32_t rk[RS ? 1 : (IPT + 1) / 2];
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const uint32_t dg = (c[j] >> sh) & (kPkRadix - 1);
@@ -504,11 +517,15 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
             uint32_t old = 0;
             if (lane == leader) {
                 old = hist[dg * HSTRIDE + wp];
-                hist[dg * HSTRIDE + wp] = old + __popc(peers);
+                hist[dg * HSTRIDE + wp] = (HT)(old + __popc(peers));
             }
             old = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
-            if (j & 1) rk[j >> 1] |= old << 16;
-            else rk[j >> 1] = old;
+            if constexpr (RS) {
+                rks[pos0 + j * 32] = (uint16_t)old;
+            } else {
+                if (j & 1) rk[j >> 1] |= old << 16;
+                else rk[j >> 1] = old;
+            }
         }
         __syncthreads();
         {
@@ -545,7 +562,7 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
                 const int lin = threadIdx.x * PER + q;
-                hist[(lin / WARPS) * HSTRIDE + (lin % WARPS)] = off;
+                hist[(lin / WARPS) * HSTRIDE + (lin % WARPS)] = (HT)off;
                 off += cnt[q];
             }
         }
@@ -553,7 +570,8 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
 #pragma unroll
         for (int j = 0; j < IPT; ++j) {
             const uint32_t dg = (c[j] >> sh) & (kPkRadix - 1);
-            skey[hist[dg * HSTRIDE + wp] + ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu)] = c[j];
+            const uint32_t r = RS ? (uint32_t)rks[pos0 + j * 32] : ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu);
+            skey[hist[dg * HSTRIDE + wp] + r] = c[j];
         }
         __syncthreads();
 #pragma unroll
@@ -638,7 +656,10 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
 
 template <int IPT, int TH>
 static size_t sort_packed_smem() {
-    return (size_t)TH * IPT * 4 + (size_t)(kPkRadix * (TH / 32 + 1) + TH * IPT / 32 + TH / 32 + 2) * 4;
+    constexpr bool RS = packed_ranks_in_smem(IPT, TH);
+    const size_t hist = (size_t)kPkRadix * (TH / 32 + 1) * (RS ? 2 : 4);
+    return (size_t)TH * IPT * 4 + (RS ? (size_t)TH * IPT * 2 : 0) + ((hist + 15) & ~(size_t)15) +
+           (size_t)(TH * IPT / 32 + TH / 32 + 2) * 4;
 }
 
 template <int IPT, int TH = kPkThreads>
