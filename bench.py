@@ -83,13 +83,15 @@ def _peak():
 
 
 def search_source_digest() -> str:
-    """SHA-256 of the plain search kernel's source: k_screen with the helpers
-    it uses in its file, and the device header."""
+    """SHA-256 of the plain search kernel's source: k_screen, the device pieces
+    it shares with the batched kernels, and the device header."""
+    csrc = os.path.dirname(SEARCH_SRC)
     src = open(SEARCH_SRC).read()
-    a = src.index("// Predicated running max/min")
+    a = src.index("template <int U>\n__global__ void __launch_bounds__")
     b = src.index("cudaError_t launch_screen(")
-    dev = open(os.path.join(os.path.dirname(SEARCH_SRC), "vjb_device.cuh")).read()
-    return hashlib.sha256((src[a:b] + dev).encode()).hexdigest()
+    shared = open(os.path.join(csrc, "k_search.cuh")).read()
+    dev = open(os.path.join(csrc, "vjb_device.cuh")).read()
+    return hashlib.sha256((shared + src[a:b] + dev).encode()).hexdigest()
 
 
 def _traffic():

@@ -19,7 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libvjb.so")
-SOURCES = ["vjb_api.cu", "vjb_batch.cu", "k_prepare.cu", "k_search.cu", "k_update.cu", "k_classify.cu"]
+SOURCES = ["vjb_api.cu", "vjb_batch.cu", "k_prepare.cu", "k_search.cu", "k_bsearch.cu", "k_update.cu",
+           "k_classify.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

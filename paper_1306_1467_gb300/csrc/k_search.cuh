@@ -1,0 +1,302 @@
+// Device pieces shared by the plain search kernels (k_search.cu) and the
+// batched ones (k_bsearch.cu): the FP32 scan of a stage of table entries and
+// the end of a row, the shortlist threshold, and the double-float re-scan of a
+// shortlisted feature with the choice of the round's stump.
+#pragma once
+
+#include <limits.h>
+#include <math.h>
+
+#include "vjb_device.cuh"
+#include "vjb_internal.cuh"
+
+namespace vjb {
+
+__host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Predicated running max/min: update only where `flag` is set (a valid split).
+__device__ __forceinline__ void minmax_if(uint32_t flag, float a, float &mx, float &mn) {
+    asm("{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %2, 0;\n\t"
+        "@p max.f32 %0, %0, %3;\n\t"
+        "@p min.f32 %1, %1, %3;\n\t}"
+        : "+f"(mx), "+f"(mn)
+        : "r"(flag), "f"(a));
+}
+
+// U pieces of CR chunk rows of a stage (8 entries per lane per chunk row),
+// worked on together for instruction-level parallelism.  Lane k reads chunk
+// t * 32 + k: its own run, in order, 16 bytes at a time, the 32 lanes covering
+// 512 contiguous bytes (no bank conflict).  Each piece is summed in FP32 from
+// zero; its largest and smallest prefix at a valid split, offset by the
+// lane's compensated running total (ahi + alo), update the lane's best
+// (bmx, bmn); then the piece total enters the running total through TwoSum.
+template <int U, int CR>
+__device__ __forceinline__ void scan_pieces(uint32_t sbase, int t0, int lane, const float *sv,
+                                            float &ahi, float &alo, float &bmx, float &bmn) {
+    constexpr int E = CR * kChunkElems;
+    uint32_t wd[U][CR * 4];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int c = 0; c < CR; ++c) {
+            const uint4 q = lds128(sbase + (uint32_t)(((t0 + u * CR + c) * 32 + lane) * 16));
+            wd[u][4 * c + 0] = q.x;
+            wd[u][4 * c + 1] = q.y;
+            wd[u][4 * c + 2] = q.z;
+            wd[u][4 * c + 3] = q.w;
+        }
+    float g[U][E];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < E / 2; ++j) {
+            g[u][2 * j] = sv[wd[u][j] & kIndexMask];  // even position: word | flag << 15
+            g[u][2 * j + 1] = sv[wd[u][j] >> 17];      // odd position: (word << 1 | flag) << 16
+        }
+    float a[U], mx[U], mn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        a[u] = 0.f;
+        mx[u] = -INFINITY;
+        mn[u] = INFINITY;
+    }
+#pragma unroll
+    for (int j = 0; j < E; ++j)
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a[u] += g[u][j];
+            const uint32_t fl = (j & 1) ? (wd[u][j >> 1] & 0x10000u) : (wd[u][j >> 1] & 0x8000u);
+            minmax_if(fl, a[u], mx[u], mn[u]);
+        }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        bmx = fmaxf(bmx, ahi + (alo + mx[u]));
+        bmn = fminf(bmn, ahi + (alo + mn[u]));
+        float sum, err;
+        two_sum(ahi, a[u], sum, err);
+        ahi = sum;
+        alo += err;
+    }
+}
+
+// ---- shared pieces of the search kernels -----------------------------------------------
+
+// All chunk rows of one stage.
+template <int U>
+__device__ __forceinline__ void scan_stage(uint32_t sbase, int crs, int lane, const float *sv,
+                                           float &ahi, float &alo, float &bmx, float &bmn) {
+    int t = 0;
+    for (; t + 2 * U <= crs; t += 2 * U) scan_pieces<U, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+    for (; t + 2 <= crs; t += 2) scan_pieces<1, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+    if (t < crs) scan_pieces<1, 1>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+}
+
+// End of a row: the runs of the lanes below come first, so an exclusive
+// double-float scan of the run totals offsets each lane's best prefixes; the
+// feature's error is min(T+ - max D, T- + min D), split 0 (D = 0) included.
+__device__ __forceinline__ float finish_row(float ahi, float alo, float bmx, float bmn, float Tp,
+                                            float Tm, int lane) {
+    DF x{ahi, alo};
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const DF y = df_shfl_up(x, d);
+        if (lane >= d) x = df_add(y, x);
+    }
+    DF excl = df_shfl_up(x, 1);
+    if (lane == 0) excl = DF{0.f, 0.f};
+    float MX = warp_max(excl.hi + (excl.lo + bmx));
+    float MN = warp_min(excl.hi + (excl.lo + bmn));
+    MX = fmaxf(MX, 0.f);
+    MN = fminf(MN, 0.f);
+    return fminf(Tp - MX, Tm + MN);
+}
+
+// The screened error within which a feature must lie of the smallest one
+// (twice the screening bound, in units of the weight total).
+__device__ __forceinline__ float shortlist_threshold(float m, const RoundState *rs) {
+    return m + kScreenMarginUlps * 5.9604644775390625e-8f * (float)(rs->t_pos + rs->t_neg);
+}
+
+// ---- compensated re-scan of shortlisted features --------------------------------------
+
+__device__ __forceinline__ bool df_eq(DF a, DF b) { return a.hi == b.hi && a.lo == b.lo; }
+
+// Lexicographic candidate order: error (double-float), feature, split, +1 first.
+__device__ __forceinline__ bool cand_less(const Candidate &a, const Candidate &b) {
+    if (a.err_hi != b.err_hi) return a.err_hi < b.err_hi;
+    if (a.err_lo != b.err_lo) return a.err_lo < b.err_lo;
+    if (a.feature != b.feature) return a.feature < b.feature;
+    if (a.split != b.split) return a.split < b.split;
+    return a.polarity > b.polarity;
+}
+
+__device__ __forceinline__ Candidate cand_shfl_xor(const Candidate &c, int d) {
+    Candidate o;
+    o.err_hi = __shfl_xor_sync(0xffffffffu, c.err_hi, d);
+    o.err_lo = __shfl_xor_sync(0xffffffffu, c.err_lo, d);
+    o.feature = __shfl_xor_sync(0xffffffffu, c.feature, d);
+    o.split = __shfl_xor_sync(0xffffffffu, c.split, d);
+    o.polarity = __shfl_xor_sync(0xffffffffu, c.polarity, d);
+    o.pad = 0;
+    return o;
+}
+
+constexpr int kRescanWarps = 32;  // one warp per lane run of the row
+
+struct RunResult {
+    DF total, mx, mn;
+    int smx, smn;
+};
+
+// One warp scans lane run k of a row in double-float: 32 chunks of 8 entries
+// at a time, lane i holding chunk u0 + i of the run.  Returns (in every lane)
+// the run total and its largest / smallest prefix at a valid split, relative
+// to the run start, with the split position (number of entries before it in
+// the whole value order) and the lowest position on ties (INT_MAX if none).
+static __device__ RunResult rescan_run(const uint16_t *__restrict__ row, int run, int k,
+                                const float *__restrict__ v, int lane) {
+    DF carry{0.f, 0.f}, bmax{-INFINITY, 0.f}, bmn{INFINITY, 0.f};
+    int smax = INT_MAX, smn = INT_MAX;
+    const int nch = run / kChunkElems;
+    for (int u0 = 0; u0 < nch; u0 += 32) {
+        const int t = u0 + lane;
+        uint32_t wd[4] = {0u, 0u, 0u, 0u};
+        const bool have = t < nch;
+        if (have) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row + (size_t)(t * 32 + k) * kChunkElems));
+            wd[0] = q.x; wd[1] = q.y; wd[2] = q.z; wd[3] = q.w;
+        }
+        DF a{0.f, 0.f}, lmx{-INFINITY, 0.f}, lmn{INFINITY, 0.f};
+        int lsx = INT_MAX, lsn = INT_MAX;
+        if (have) {
+#pragma unroll
+            for (int j = 0; j < kChunkElems; ++j) {
+                const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
+                a = df_add_f(a, __ldg(v + entry_word(e, j)));
+                if (entry_flag(e, j)) {
+                    const int pos = k * run + t * kChunkElems + j + 1;
+                    if (df_less(lmx, a)) { lmx = a; lsx = pos; }
+                    if (df_less(a, lmn)) { lmn = a; lsn = pos; }
+                }
+            }
+        }
+        DF x = a;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const DF y = df_shfl_up(x, d);
+            if (lane >= d) x = df_add(y, x);
+        }
+        DF excl = df_shfl_up(x, 1);
+        if (lane == 0) excl = DF{0.f, 0.f};
+        const DF tot = df_shfl(x, 31);
+        const DF offs = df_add(carry, excl);
+        if (lsx != INT_MAX) {
+            const DF c = df_add(offs, lmx);
+            if (df_less(bmax, c)) { bmax = c; smax = lsx; }
+        }
+        if (lsn != INT_MAX) {
+            const DF c = df_add(offs, lmn);
+            if (df_less(c, bmn)) { bmn = c; smn = lsn; }
+        }
+        carry = df_add(carry, tot);
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        const DF om = df_shfl_xor(bmax, d);
+        const int os = __shfl_xor_sync(0xffffffffu, smax, d);
+        if (df_less(bmax, om) || (df_eq(om, bmax) && os < smax)) { bmax = om; smax = os; }
+        const DF on = df_shfl_xor(bmn, d);
+        const int on_s = __shfl_xor_sync(0xffffffffu, smn, d);
+        if (df_less(on, bmn) || (df_eq(on, bmn) && on_s < smn)) { bmn = on; smn = on_s; }
+    }
+    RunResult r;
+    r.total = carry;
+    r.mx = bmax;
+    r.mn = bmn;
+    r.smx = smax;
+    r.smn = smn;
+    return r;
+}
+
+// The whole CTA (kRescanWarps warps) re-scans feature f of job J; thread 0
+// returns its best (error, split, polarity).  `rres` is 32 slots of shared memory.
+static __device__ Candidate rescan_feature(const JobDesc &J, int32_t f, RunResult *rres) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int run = J.npad / 32;
+    const uint16_t *row = J.rows + (size_t)f * J.npad;
+    for (int k = warp; k < 32; k += kRescanWarps) {
+        const RunResult r = rescan_run(row, run, k, J.v, lane);
+        if (lane == 0) rres[k] = r;
+    }
+    __syncthreads();
+    Candidate cd;
+    cd.err_hi = INFINITY; cd.err_lo = 0.f; cd.feature = f; cd.split = 0; cd.polarity = 1; cd.pad = 0;
+    if (threadIdx.x == 0) {
+        const DF Tp = df_from_double(J.rs->t_pos), Tm = df_from_double(J.rs->t_neg);
+        DF offs{0.f, 0.f}, bmax{0.f, 0.f}, bmn{0.f, 0.f};  // split 0: D = 0
+        int smax = 0, smn = 0;
+        for (int k = 0; k < 32; ++k) {  // runs in value order
+            const RunResult &q = rres[k];
+            if (q.smx != INT_MAX) {
+                const DF cc = df_add(offs, q.mx);
+                if (df_less(bmax, cc)) { bmax = cc; smax = q.smx; }
+            }
+            if (q.smn != INT_MAX) {
+                const DF cc = df_add(offs, q.mn);
+                if (df_less(cc, bmn)) { bmn = cc; smn = q.smn; }
+            }
+            offs = df_add(offs, q.total);
+        }
+        const DF ep = df_add(Tp, df_neg(bmax));
+        const DF em = df_add(Tm, bmn);
+        const bool minus = df_less(em, ep) || (df_eq(em, ep) && smn < smax);
+        cd.err_hi = minus ? em.hi : ep.hi;
+        cd.err_lo = minus ? em.lo : ep.lo;
+        cd.split = minus ? smn : smax;
+        cd.polarity = minus ? -1 : 1;
+    }
+    __syncthreads();
+    return cd;
+}
+
+// The whole CTA picks job J's stump among its `cnt` re-scanned candidates.
+static __device__ void select_stump(const JobDesc &J, int cnt) {
+    __shared__ Candidate wc[kRescanWarps];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    Candidate b;
+    b.err_hi = INFINITY; b.err_lo = 0.f; b.feature = INT_MAX; b.split = INT_MAX; b.polarity = 1; b.pad = 0;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+        Candidate c;
+        const volatile Candidate *vc = J.cands + k;
+        c.err_hi = vc->err_hi; c.err_lo = vc->err_lo; c.feature = vc->feature;
+        c.split = vc->split; c.polarity = vc->polarity; c.pad = 0;
+        if (cand_less(c, b)) b = c;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        const Candidate o = cand_shfl_xor(b, d);
+        if (cand_less(o, b)) b = o;
+    }
+    if (lane == 0) wc[warp] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < kRescanWarps; ++w)
+            if (cand_less(wc[w], b)) b = wc[w];
+        RoundState *rs = J.rs;
+        if (cnt == 0 || b.feature == INT_MAX) {
+            rs->flags |= kFlagNoCandidate;
+            rs->status = VJB_EDEVICE;
+        } else {
+            rs->win_feature = b.feature;
+            rs->win_split = b.split;
+            rs->win_polarity = b.polarity;
+            rs->win_err_hi = b.err_hi;
+            rs->win_err_lo = b.err_lo;
+        }
+        rs->done_rescan = 0u;
+    }
+    __syncthreads();
+}
+
+}  // namespace vjb

@@ -385,11 +385,12 @@ def test_strong_classifier_matches_oracle(tiny_prepared):
             tr.classify(px, [dict(stumps[0], feature=10 ** 7)])
 
 
-@pytest.mark.parametrize("n_pos,n_neg", [(6000, 12000), (3000, 13383), (9000, 23000)])
+@pytest.mark.parametrize("n_pos,n_neg", [(6000, 12000), (3000, 13383), (9000, 23766)])
 def test_large_n_partial_second_copy(n_pos, n_neg):
     """N above 16,351: the second weight copy covers only the samples that fit
     15-bit word offsets (none at N close to 32,767).  Sorted rows bit-exact,
-    screened errors within the screening bound, same-input parity of rounds."""
+    screened errors within the screening bound, same-input parity of rounds.
+    32,766 is the largest N the table's 15-bit words allow."""
     from paper_1306_1467_gb300 import vjb
     px, y = synth.make_windows(n_pos, n_neg, 8, 8, seed=n_pos + n_neg)
     P = O.Prepared(px, y)
