@@ -425,12 +425,8 @@ static cudaError_t launch_sort_ipt(const int32_t *ii_t, int ii_stride, int w, co
 // after the CTA-wide scan needs only the scanned offsets.
 constexpr int kPkThreads = 512;
 constexpr int kPkRefinePasses = 1;  // a second pass buys no search time
-constexpr int kPkWarps = kPkThreads / 32;
 constexpr int kPkDigitBits = 9;
 constexpr int kPkRadix = 1 << kPkDigitBits;
-constexpr int kPkHistStride = kPkWarps + 1;
-constexpr int kPkHistWords = kPkRadix * kPkHistStride;
-static_assert(kPkThreads * 32 / 4 <= kPkHistWords, "histogram space too small for bank loads");
 
 __host__ __device__ constexpr bool packed_ranks_in_smem(int ipt, int th) { return th <= 512 && ipt >= 20 && ipt <= 30; }
 
@@ -442,6 +438,8 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
     constexpr int NP = TH * IPT;
     constexpr int WARPS = TH / 32, HSTRIDE = WARPS + 1, HWORDS = kPkRadix * HSTRIDE;
     constexpr int GROUPS = NP / 32;  // lane-run groups of the longest row
+    static_assert(3 * GROUPS * 4 <= HWORDS * (packed_ranks_in_smem(IPT, TH) ? 2 : 4),
+                  "histogram space too small for the refine list");
     // 512-thread CTAs of 20 to 30 items keep the items' ranks in shared memory
     // (registers would spill) and count in 16 bits (counts and offsets stay
     // below 2^16) so that two CTAs still fit an SM; the others keep them in
@@ -609,35 +607,54 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
     if (L.dual) {
         // bank-balanced copy choice per gather group (see k_sort_rows); the
         // loads of the 32 banks live in registers as 2-bit counters, banks
-        // 0-15 in cl and 16-31 in ch (a load above 3 counts as 3)
+        // 0-15 in cl and 16-31 in ch (a load above 3 counts as 3).  Only the
+        // groups left with a bank at 3 after the greedy pass get the pass of
+        // single moves; they are listed first (in the free histogram space) so
+        // that the threads share them evenly.
+        auto level = [](uint32_t cl, uint32_t ch, int b) { return ((b < 16 ? cl : ch) >> (2 * (b & 15))) & 3u; };
+        auto inc = [&](uint32_t &cl, uint32_t &ch, int b) {
+            if (level(cl, ch, b) == 3u) return;
+            const uint32_t one = 1u << (2 * (b & 15));
+            if (b < 16) cl += one;
+            else ch += one;
+        };
+        auto dec = [&](uint32_t &cl, uint32_t &ch, int b) {
+            if (level(cl, ch, b) == 0u) return;
+            const uint32_t one = 1u << (2 * (b & 15));
+            if (b < 16) cl -= one;
+            else ch -= one;
+        };
+        uint32_t *rlist = reinterpret_cast<uint32_t *>(hist);  // (group, cl, ch) of groups to refine
+        if (threadIdx.x == 0) mm[0] = 0;
+        __syncthreads();
         for (int g = threadIdx.x; g < run; g += TH) {
             uint32_t cl = 0, ch = 0, mask = 0;
-            auto level = [&](int b) { return ((b < 16 ? cl : ch) >> (2 * (b & 15))) & 3u; };
-            auto inc = [&](int b) {
-                if (level(b) == 3u) return;
-                const uint32_t one = 1u << (2 * (b & 15));
-                if (b < 16) cl += one;
-                else ch += one;
-            };
-            auto dec = [&](int b) {
-                if (level(b) == 0u) return;
-                const uint32_t one = 1u << (2 * (b & 15));
-                if (b < 16) cl -= one;
-                else ch -= one;
-            };
             bool pad_seen = false;
             for (int k = 0; k < 32; ++k) {
                 const int p = k * run + g;
                 if (p >= n) {
-                    if (!pad_seen) inc(n & 31);  // the padding word, read as a broadcast
+                    if (!pad_seen) inc(cl, ch, n & 31);  // the padding word, read as a broadcast
                     pad_seen = true;
                     continue;
                 }
                 const int i = (int)(skey[p] & imask);
                 const int ba = i & 31, bb = rot_b(i) & 31;
-                if (i < L.nb && level(bb) < level(ba)) { inc(bb); mask |= 1u << k; }
-                else inc(ba);
+                if (i < L.nb && level(cl, ch, bb) < level(cl, ch, ba)) { inc(cl, ch, bb); mask |= 1u << k; }
+                else inc(cl, ch, ba);
             }
+            gchoice[g] = mask;
+            if (kPkRefinePasses > 0 && (((cl & (cl >> 1)) | (ch & (ch >> 1))) & 0x55555555u)) {
+                const int q = atomicAdd(&mm[0], 1);
+                rlist[3 * q] = (uint32_t)g;
+                rlist[3 * q + 1] = cl;
+                rlist[3 * q + 2] = ch;
+            }
+        }
+        __syncthreads();
+        const int nref = mm[0];
+        for (int q = threadIdx.x; q < nref; q += TH) {
+            const int g = (int)rlist[3 * q];
+            uint32_t cl = rlist[3 * q + 1], ch = rlist[3 * q + 2], mask = gchoice[g];
             for (int pass = 0; pass < kPkRefinePasses; ++pass)
                 for (int k = 0; k < 32; ++k) {
                     const int p = k * run + g;
@@ -647,9 +664,9 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
                     const int ba = i & 31, bb = rot_b(i) & 31;
                     const bool onb = (mask >> k) & 1u;
                     const int cur = onb ? bb : ba, oth = onb ? ba : bb;
-                    if (level(cur) > level(oth) + 1) {
-                        dec(cur);
-                        inc(oth);
+                    if (level(cl, ch, cur) > level(cl, ch, oth) + 1) {
+                        dec(cl, ch, cur);
+                        inc(cl, ch, oth);
                         mask ^= 1u << k;
                     }
                 }

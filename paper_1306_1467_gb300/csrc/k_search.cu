@@ -15,8 +15,8 @@
 //  * k_screen (the hot kernel): streams the whole uint16 table once per round
 //    with TMA, gathers v from shared memory, and forms D with FP32 prefix sums.
 //    A warp scans one row: lane k walks its own run of the value order (the
-//    row layout interleaves 32 runs), summing 16 entries at a time in FP32 and
-//    folding each piece into a compensated (TwoSum) running total; one
+//    row layout interleaves 32 runs), summing 16 or 24 entries at a time in
+//    FP32 and folding each piece into a compensated (TwoSum) running total; one
 //    double-float warp scan of the 32 run totals per row places every lane's
 //    best prefix in the row.  It writes each feature's FP32 error and each
 //    CTA's minimum.
@@ -28,11 +28,11 @@
 //    picks the round's stump: lowest error, then feature, split, +1 before -1.
 //
 // Screening error bound (u = 2^-24, sum |v| = T+ + T- = 1 after normalising):
-// a piece's partial sums of at most 16 terms err by at most 16u times the
+// a piece's partial sums of at most 24 terms err by at most 24u times the
 // piece's |v| mass; the compensated run total and the double-float scan of run
 // totals add O(u^2); placing the piece's extreme on the run total, and that on
 // the run offset, adds 4u |D|; forming T+- -/+ D in FP32 adds 2u.  So
-// |screened - exact| <= 22u.  A margin of 64u (twice 32u) keeps every
+// |screened - exact| <= 30u.  A margin of 64u (twice 32u) keeps every
 // feature that could beat the best one.
 #include <limits.h>
 #include <math.h>

@@ -82,12 +82,18 @@ __device__ __forceinline__ void scan_pieces(uint32_t sbase, int t0, int lane, co
 
 // ---- shared pieces of the search kernels -----------------------------------------------
 
-// All chunk rows of one stage.
+// All chunk rows of one stage, 2U chunk rows (16U entries per lane) at a
+// time: U pieces of 16 entries, or with U = 3 two pieces of 24 (fewer piece
+// ends to fold in; 24 terms keep the screening bound of k_search.cu).
 template <int U>
 __device__ __forceinline__ void scan_stage(uint32_t sbase, int crs, int lane, const float *sv,
                                            float &ahi, float &alo, float &bmx, float &bmn) {
     int t = 0;
-    for (; t + 2 * U <= crs; t += 2 * U) scan_pieces<U, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+    if constexpr (U == 3) {
+        for (; t + 6 <= crs; t += 6) scan_pieces<2, 3>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+    } else {
+        for (; t + 2 * U <= crs; t += 2 * U) scan_pieces<U, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+    }
     for (; t + 2 <= crs; t += 2) scan_pieces<1, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
     if (t < crs) scan_pieces<1, 1>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
 }
