@@ -95,23 +95,25 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
     }
     __syncthreads();
 
-    const int64_t gw = (int64_t)blockIdx.x * nw + warp;
-    const int64_t G = (int64_t)gridDim.x * nw;
-    const int64_t nf_w = gw < nfeat ? (nfeat - 1 - gw) / G + 1 : 0;
+    // rows gw, gw + G, ... of this warp; feature indices fit int32 (nfeat <
+    // 2^31), and so does the warp's chunk count (G >= 152 warps, at most 128
+    // chunks per row)
+    const int gw = blockIdx.x * nw + warp;
+    const int G = gridDim.x * nw;
+    const int nf_w = gw < nfeat ? (int)((nfeat - 1 - gw) / G) + 1 : 0;
     const int nc = (lines_per_row + box_lines - 1) / box_lines;
-    const int64_t total = nf_w * nc;
+    const int total = nf_w * nc;
     const uint32_t tx = (uint32_t)box_lines * kLineBytes;
 
     // producer state (lane 0): the next chunk to load, in this warp's order
-    int64_t pk = 0, issued = 0;
-    int pc = 0, pstage = 0;
+    int issued = 0, prow = gw, pline = 0, pstage = 0;
+    const int last_line = (nc - 1) * box_lines;
     auto issue_next = [&]() {
         if (issued >= total) return;
         const uint32_t bar = bar_w + 8u * (uint32_t)pstage;
         mbar_arrive_expect_tx(bar, tx);
-        tma_load_3d(ring_w + (uint32_t)pstage * stage_bytes, &tmap, 0, pc * box_lines,
-                    (int32_t)(gw + pk * G), bar);
-        if (++pc == nc) { pc = 0; ++pk; }
+        tma_load_3d(ring_w + (uint32_t)pstage * stage_bytes, &tmap, 0, pline, prow, bar);
+        if (pline == last_line) { pline = 0; prow += G; } else { pline += box_lines; }
         if (++pstage == stages) pstage = 0;
         ++issued;
     };
@@ -123,20 +125,20 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
     float best = INFINITY;
     int cstage = 0;
     uint32_t cpar = 0;  // consumer ring position and mbarrier phase
-    int64_t consumed = 0;
+    int consumed = 0;
     bool ok = true;
-    for (int64_t k = 0; k < nf_w && ok; ++k) {
-        const int64_t f = gw + k * G;
+    const int crs_full = box_lines >> 2;                          // chunk rows of a full stage
+    const int crs_last = (lines_per_row - (nc - 1) * box_lines) >> 2;  // and of a row's last one
+    for (int k = 0; k < nf_w && ok; ++k) {
+        const int f = gw + k * G;
         float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
         for (int c = 0; c < nc; ++c) {
             if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
                 ok = false;
                 break;
             }
-            const int lines_here = min(box_lines, lines_per_row - c * box_lines);
-            const int crs = lines_here >> 2;  // chunk rows (a line is a quarter of one)
             const uint32_t sbase = ring_w + (uint32_t)cstage * stage_bytes;
-            scan_stage<U>(sbase, crs, lane, sv, ahi, alo, bmx, bmn);
+            scan_stage<U>(sbase, c == nc - 1 ? crs_last : crs_full, lane, sv, ahi, alo, bmx, bmn);
             __syncwarp();
             if (lane == 0) {
                 fence_proxy_async_smem();
@@ -159,8 +161,8 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
             // chunks issued but not consumed sit in the ring from the current stage on
             int st = cstage;
             uint32_t ph = cpar;
-            const int64_t pending = issued - consumed;
-            for (int64_t s = 0; s < pending; ++s) {
+            const int pending = issued - consumed;
+            for (int s = 0; s < pending; ++s) {
                 mbar_wait_bounded(bar_w + 8u * (uint32_t)st, ph, 100000000ull);
                 if (++st == stages) { st = 0; ph ^= 1u; }
             }
