@@ -147,10 +147,11 @@ int take_events(vjb_ctx *c, EventTriple &t) {
 
 // Fold finished event triples into the timing totals (the stream must be idle).
 int collect_timing(vjb_ctx *c) {
-    for (auto &t : c->ev_pending) {
+    for (auto &p : c->ev_pending) {
+        const EventTriple &t = p.ev;
         float a = 0.f, b = 0.f;
         CK(cudaEventElapsedTime(&a, t[0], t[1]));
-        CK(cudaEventElapsedTime(&b, t[0], t[2]));
+        CK(cudaEventElapsedTime(&b, t[0], p.end));
         if (c->tacc.rounds == 0) {
             c->tacc.search_ms_min = a;
             c->tacc.search_ms_max = a;
@@ -204,65 +205,65 @@ int enqueue_update(vjb_ctx *c) {
     return VJB_OK;
 }
 
-int enqueue_round(vjb_ctx *c, const EventTriple *ev, unsigned rec_flags) {
-    if (ev) CK(cudaEventRecordWithFlags((*ev)[0], c->stream, rec_flags));
+// The search kernel of a round, then the rest (shortlist, re-scan, update).
+int enqueue_search(vjb_ctx *c) {
     CK(launch_screen(&c->tmap, c->d_v, c->lay, c->lines, c->box_lines, c->nfeat, c->shape,
                      c->screen_grid, c->d_rs, c->d_ferr, c->d_bmin, c->stream));
-    if (ev) CK(cudaEventRecordWithFlags((*ev)[1], c->stream, rec_flags));
-    const JobDesc J = job_desc(c);
-    CK(launch_shortlist(J, c->d_bmin, c->screen_grid, c->shortlist_grid, c->stream));
-    CK(launch_rescan(J, c->rescan_grid, c->stream));
-    int rc = enqueue_update(c);
-    if (rc) return rc;
-    if (ev) CK(cudaEventRecordWithFlags((*ev)[2], c->stream, rec_flags));
     return VJB_OK;
 }
 
-int ensure_graph(vjb_ctx *c) {
-    if (c->gexec && c->graph_timed == c->timing) return VJB_OK;
-    c->drop_graph();
-    EventTriple cap{};
-    if (c->timing) {
-        int rc = take_events(c, cap);
-        if (rc) return rc;
-    }
+int enqueue_tail(vjb_ctx *c) {
+    const JobDesc J = job_desc(c);
+    CK(launch_shortlist(J, c->d_bmin, c->screen_grid, c->shortlist_grid, c->stream));
+    CK(launch_rescan(J, c->rescan_grid, c->stream));
+    return enqueue_update(c);
+}
+
+int enqueue_round(vjb_ctx *c, const EventTriple *ev) {
+    if (ev) CK(cudaEventRecord((*ev)[0], c->stream));
+    int rc = enqueue_search(c);
+    if (rc) return rc;
+    if (ev) CK(cudaEventRecord((*ev)[1], c->stream));
+    rc = enqueue_tail(c);
+    if (rc) return rc;
+    if (ev) CK(cudaEventRecord((*ev)[2], c->stream));
+    return VJB_OK;
+}
+
+// Capture `part` of a round (0 the whole round, 1 the search, 2 the rest) as
+// an instantiated graph.
+int capture_round(vjb_ctx *c, int part, cudaGraph_t *graph, cudaGraphExec_t *exec) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_round(c, c->timing ? &cap : nullptr, cudaEventRecordExternal);
+    int rc = part == 1 ? enqueue_search(c) : (part == 2 ? enqueue_tail(c) : enqueue_round(c, nullptr));
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-    if (c->timing) c->ev_free.push_back(cap);
     if (rc != VJB_OK) {
         if (g) cudaGraphDestroy(g);
         return rc;
     }
     if (e != cudaSuccess) return fail(VJB_ECUDA, "graph capture failed: %s", cudaGetErrorString(e));
-    if (c->timing) {
-        size_t nn = 0;
-        CK(cudaGraphGetNodes(g, nullptr, &nn));
-        std::vector<cudaGraphNode_t> nodes(nn);
-        CK(cudaGraphGetNodes(g, nodes.data(), &nn));
-        int found = 0;
-        for (auto nd : nodes) {
-            cudaGraphNodeType ty;
-            CK(cudaGraphNodeGetType(nd, &ty));
-            if (ty != cudaGraphNodeTypeEventRecord) continue;
-            cudaEvent_t ev;
-            CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
-            for (int k = 0; k < 3; ++k)
-                if (ev == cap[k]) { c->ev_nodes[k] = nd; ++found; }
-        }
-        if (found != 3) {
-            cudaGraphDestroy(g);
-            return fail(VJB_ECUDA, "timed graph has %d of 3 event nodes", found);
-        }
-    }
-    e = cudaGraphInstantiate(&c->gexec, g, 0);
+    e = cudaGraphInstantiate(exec, g, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
-        c->gexec = nullptr;
+        *exec = nullptr;
         return fail(VJB_ECUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     }
-    c->graph = g;
+    *graph = g;
+    return VJB_OK;
+}
+
+// The round as one graph; with timing on, as two (the search and the rest)
+// with the timing events recorded on the stream around them, so that no
+// graph is updated between replays.
+int ensure_graph(vjb_ctx *c) {
+    if (c->gexec && c->graph_timed == c->timing) return VJB_OK;
+    c->drop_graph();
+    int rc = capture_round(c, c->timing ? 1 : 0, &c->graph, &c->gexec);
+    if (rc == VJB_OK && c->timing) rc = capture_round(c, 2, &c->graph2, &c->gexec2);
+    if (rc != VJB_OK) {
+        c->drop_graph();
+        return rc;
+    }
     c->graph_timed = c->timing;
     return VJB_OK;
 }
@@ -524,10 +525,10 @@ int vjb_train_round(vjb_ctx *c, vjb_stump *out) {
             rc = take_events(c, ev);
             if (rc) return rc;
         }
-        rc = enqueue_round(c, c->timing ? &ev : nullptr, cudaEventRecordDefault);
+        rc = enqueue_round(c, c->timing ? &ev : nullptr);
         if (rc) return rc;
         c->launches += kRoundLaunches;
-        if (c->timing) c->ev_pending.push_back(ev);
+        if (c->timing) c->ev_pending.push_back(PendingRound{ev, ev[2]});
         rc = read_state(c, &rs);
         if (rc) return rc;
     }
@@ -555,14 +556,21 @@ int vjb_train_strong(vjb_ctx *c, int32_t T, vjb_stump *out, int32_t *rounds_done
         if (rc) return rc;
         for (int32_t t = 0; t < T; ++t) {
             if (c->timing) {
+                // two events per round: a round ends where the next one
+                // starts; the last one records its own end
                 EventTriple ev{};
                 rc = take_events(c, ev);
                 if (rc) return rc;
-                for (int k = 0; k < 3; ++k)
-                    CK(cudaGraphExecEventRecordNodeSetEvent(c->gexec, c->ev_nodes[k], ev[k]));
-                c->ev_pending.push_back(ev);
+                CK(cudaEventRecord(ev[0], c->stream));
+                if (t > 0) c->ev_pending.back().end = ev[0];
+                CK(cudaGraphLaunch(c->gexec, c->stream));
+                CK(cudaEventRecord(ev[1], c->stream));
+                CK(cudaGraphLaunch(c->gexec2, c->stream));
+                if (t == T - 1) CK(cudaEventRecord(ev[2], c->stream));
+                c->ev_pending.push_back(PendingRound{ev, ev[2]});
+            } else {
+                CK(cudaGraphLaunch(c->gexec, c->stream));
             }
-            CK(cudaGraphLaunch(c->gexec, c->stream));
             c->launches += kRoundLaunches;
         }
         rc = read_state(c, &rs);
@@ -849,7 +857,7 @@ int vjb_set_timing(vjb_ctx *c, int32_t enable) {
     int rc = set_dev(c);
     if (rc) return rc;
     CK(cudaStreamSynchronize(c->stream));
-    for (auto &t : c->ev_pending) c->ev_free.push_back(t);
+    for (auto &t : c->ev_pending) c->ev_free.push_back(t.ev);
     c->ev_pending.clear();
     c->tacc = vjb_timing{};
     c->timing = enable != 0;

@@ -41,21 +41,23 @@ struct vjb_batch {
     bool dirty = true;  // the device job table must be rebuilt
     SearchShape shape{16, 2, 1, 3, 24};
     int rows_per_warp = VJB_BATCH_INTERLEAVED;  // the schedule; > 0: work queue of that many rows per warp
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    // the round graph; with timing on, the search (graph) and the rest
+    // (graph2), launched with the timing events (round start, search end,
+    // round end) recorded on the stream between them
+    cudaGraph_t graph = nullptr, graph2 = nullptr;
+    cudaGraphExec_t gexec = nullptr, gexec2 = nullptr;
     int64_t launches = 0;
-    // with timing on, the round graph holds three event-record nodes (round
-    // start, search end, round end) given fresh events at every replay
     bool timing = false, graph_timed = false;
-    cudaGraphNode_t ev_nodes[3] = {nullptr, nullptr, nullptr};
     std::vector<EventTriple> ev_free, ev_pending;
     vjb_timing tacc{};
 
     void drop_graph() {
         if (gexec) cudaGraphExecDestroy(gexec);
+        if (gexec2) cudaGraphExecDestroy(gexec2);
         if (graph) cudaGraphDestroy(graph);
-        gexec = nullptr;
-        graph = nullptr;
+        if (graph2) cudaGraphDestroy(graph2);
+        gexec = gexec2 = nullptr;
+        graph = graph2 = nullptr;
     }
 };
 
@@ -169,18 +171,21 @@ int batch_sync(vjb_batch *b) {
     return VJB_OK;
 }
 
-int batch_enqueue_round(vjb_batch *b, const EventTriple *ev) {
+// Part 1 of a batched round (begin + search), part 2 (shortlist, re-scan,
+// update), or 0 for both.
+int batch_enqueue_round(vjb_batch *b, int part) {
     const int g = b->num_sms;
-    if (ev) CK(cudaEventRecordWithFlags((*ev)[0], b->stream, cudaEventRecordExternal));
-    CK(launch_bbegin(b->d_jobs, b->d_meta, b->stream));
-    CK(launch_bscreen(b->maps, b->d_jobs, b->d_items, b->d_meta, kBatchMaxWords, b->shape,
-                      b->rows_per_warp, g * b->shape.ctas_per_sm, b->stream));
-    if (ev) CK(cudaEventRecordWithFlags((*ev)[1], b->stream, cudaEventRecordExternal));
-    CK(launch_bshortlist(b->d_jobs, b->d_meta, g * 4, b->stream));
-    CK(launch_brescan(b->d_jobs, b->d_meta, std::min(g, 128), b->stream));
-    CK(launch_bupdate_a(b->d_jobs, b->d_meta, g * 4, b->stream));
-    CK(launch_bupdate_b(b->d_jobs, b->d_meta, g * 4, b->stream));
-    if (ev) CK(cudaEventRecordWithFlags((*ev)[2], b->stream, cudaEventRecordExternal));
+    if (part != 2) {
+        CK(launch_bbegin(b->d_jobs, b->d_meta, b->stream));
+        CK(launch_bscreen(b->maps, b->d_jobs, b->d_items, b->d_meta, kBatchMaxWords, b->shape,
+                          b->rows_per_warp, g * b->shape.ctas_per_sm, b->stream));
+    }
+    if (part != 1) {
+        CK(launch_bshortlist(b->d_jobs, b->d_meta, g * 4, b->stream));
+        CK(launch_brescan(b->d_jobs, b->d_meta, std::min(g, 128), b->stream));
+        CK(launch_bupdate_a(b->d_jobs, b->d_meta, g * 4, b->stream));
+        CK(launch_bupdate_b(b->d_jobs, b->d_meta, g * 4, b->stream));
+    }
     return VJB_OK;
 }
 
@@ -212,51 +217,35 @@ int batch_collect_timing(vjb_batch *b) {
     return VJB_OK;
 }
 
-int batch_ensure_graph(vjb_batch *b) {
-    if (b->gexec && b->graph_timed == b->timing) return VJB_OK;
-    b->drop_graph();
-    EventTriple cap{};
-    if (b->timing) {
-        const int rc = batch_take_events(b, cap);
-        if (rc) return rc;
-    }
+int batch_capture(vjb_batch *b, int part, cudaGraph_t *graph, cudaGraphExec_t *exec) {
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = batch_enqueue_round(b, b->timing ? &cap : nullptr);
+    const int rc = batch_enqueue_round(b, part);
     cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-    if (b->timing) b->ev_free.push_back(cap);
     if (rc) {
         if (g) cudaGraphDestroy(g);
         return rc;
     }
     if (e != cudaSuccess) return fail(VJB_ECUDA, "batch graph capture failed: %s", cudaGetErrorString(e));
-    if (b->timing) {
-        size_t nn = 0;
-        CK(cudaGraphGetNodes(g, nullptr, &nn));
-        std::vector<cudaGraphNode_t> nodes(nn);
-        CK(cudaGraphGetNodes(g, nodes.data(), &nn));
-        int found = 0;
-        for (auto nd : nodes) {
-            cudaGraphNodeType ty;
-            CK(cudaGraphNodeGetType(nd, &ty));
-            if (ty != cudaGraphNodeTypeEventRecord) continue;
-            cudaEvent_t ev;
-            CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
-            for (int k = 0; k < 3; ++k)
-                if (ev == cap[k]) { b->ev_nodes[k] = nd; ++found; }
-        }
-        if (found != 3) {
-            cudaGraphDestroy(g);
-            return fail(VJB_ECUDA, "timed batch graph has %d of 3 event nodes", found);
-        }
-    }
-    e = cudaGraphInstantiate(&b->gexec, g, 0);
+    e = cudaGraphInstantiate(exec, g, 0);
     if (e != cudaSuccess) {
         cudaGraphDestroy(g);
-        b->gexec = nullptr;
+        *exec = nullptr;
         return fail(VJB_ECUDA, "batch graph instantiate failed: %s", cudaGetErrorString(e));
     }
-    b->graph = g;
+    *graph = g;
+    return VJB_OK;
+}
+
+int batch_ensure_graph(vjb_batch *b) {
+    if (b->gexec && b->graph_timed == b->timing) return VJB_OK;
+    b->drop_graph();
+    int rc = batch_capture(b, b->timing ? 1 : 0, &b->graph, &b->gexec);
+    if (rc == VJB_OK && b->timing) rc = batch_capture(b, 2, &b->graph2, &b->gexec2);
+    if (rc) {
+        b->drop_graph();
+        return rc;
+    }
     b->graph_timed = b->timing;
     return VJB_OK;
 }
@@ -307,10 +296,15 @@ int batch_run(vjb_batch *b, int R, float *ms) {
                 EventTriple ev;
                 rc = batch_take_events(b, ev);
                 if (rc) return rc;
-                for (int k = 0; k < 3; ++k) CK(cudaGraphExecEventRecordNodeSetEvent(b->gexec, b->ev_nodes[k], ev[k]));
+                CK(cudaEventRecord(ev[0], b->stream));
+                CK(cudaGraphLaunch(b->gexec, b->stream));
+                CK(cudaEventRecord(ev[1], b->stream));
+                CK(cudaGraphLaunch(b->gexec2, b->stream));
+                CK(cudaEventRecord(ev[2], b->stream));
                 b->ev_pending.push_back(ev);
+            } else {
+                CK(cudaGraphLaunch(b->gexec, b->stream));
             }
-            CK(cudaGraphLaunch(b->gexec, b->stream));
             b->launches += 6;
         }
         if (ms) {

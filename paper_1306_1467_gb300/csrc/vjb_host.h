@@ -57,6 +57,12 @@ constexpr int kStageNone = 0, kStageLoaded = 1, kStageIntegral = 2, kStagePrepar
 constexpr int kRoundLaunches = 5;  // screen, shortlist, rescan, update a, update b
 
 using EventTriple = std::array<cudaEvent_t, 3>;  // round start, search end, round end
+// A timed round: its events and the one that ends it (its own third event, or
+// the next round's start when rounds follow each other in one call).
+struct PendingRound {
+    EventTriple ev;
+    cudaEvent_t end;
+};
 
 }  // namespace vjb
 
@@ -103,21 +109,24 @@ struct vjb_ctx {
     bool shape_set = false;
     int screen_grid = 0, shortlist_grid = 0, rescan_grid = 0;
 
-    // graph of one round; with timing on it holds three event-record nodes
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t gexec = nullptr;
+    // graph of one round; with timing on, of its search (graph) and of the
+    // rest (graph2), launched with the timing events between them
+    cudaGraph_t graph = nullptr, graph2 = nullptr;
+    cudaGraphExec_t gexec = nullptr, gexec2 = nullptr;
     bool graph_timed = false;
-    cudaGraphNode_t ev_nodes[3] = {nullptr, nullptr, nullptr};
 
     bool timing = false;
-    std::vector<EventTriple> ev_free, ev_pending;
+    std::vector<EventTriple> ev_free;
+    std::vector<PendingRound> ev_pending;
     vjb_timing tacc{};
 
     void drop_graph() {
         if (gexec) cudaGraphExecDestroy(gexec);
+        if (gexec2) cudaGraphExecDestroy(gexec2);
         if (graph) cudaGraphDestroy(graph);
-        gexec = nullptr;
-        graph = nullptr;
+        if (graph2) cudaGraphDestroy(graph2);
+        gexec = gexec2 = nullptr;
+        graph = graph2 = nullptr;
     }
     void free_all() {
         drop_graph();
@@ -138,7 +147,7 @@ struct vjb_ctx {
     }
     void free_events() {
         for (auto &t : ev_free) for (auto e : t) cudaEventDestroy(e);
-        for (auto &t : ev_pending) for (auto e : t) cudaEventDestroy(e);
+        for (auto &t : ev_pending) for (auto e : t.ev) cudaEventDestroy(e);
         ev_free.clear();
         ev_pending.clear();
     }
