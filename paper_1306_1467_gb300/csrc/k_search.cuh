@@ -148,7 +148,7 @@ __device__ __forceinline__ Candidate cand_shfl_xor(const Candidate &c, int d) {
     return o;
 }
 
-constexpr int kRescanWarps = 32;  // one warp per lane run of the row
+constexpr int kRescanWarps = 32;  // one warp per lane run of the row (select_stump relies on 32)
 
 struct RunResult {
     DF total, mx, mn;
@@ -165,14 +165,17 @@ static __device__ RunResult rescan_run(const uint16_t *__restrict__ row, int run
     DF carry{0.f, 0.f}, bmax{-INFINITY, 0.f}, bmn{INFINITY, 0.f};
     int smax = INT_MAX, smn = INT_MAX;
     const int nch = run / kChunkElems;
+    auto load_chunk = [&](int t) {
+        return t < nch ? __ldg(reinterpret_cast<const uint4 *>(row + (size_t)(t * 32 + k) * kChunkElems))
+                       : make_uint4(0u, 0u, 0u, 0u);
+    };
+    uint4 qn = load_chunk(lane);  // the next 32 chunks load while these are scanned
     for (int u0 = 0; u0 < nch; u0 += 32) {
         const int t = u0 + lane;
-        uint32_t wd[4] = {0u, 0u, 0u, 0u};
+        const uint4 q = qn;
+        if (u0 + 32 < nch) qn = load_chunk(t + 32);
+        const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
         const bool have = t < nch;
-        if (have) {
-            const uint4 q = __ldg(reinterpret_cast<const uint4 *>(row + (size_t)(t * 32 + k) * kChunkElems));
-            wd[0] = q.x; wd[1] = q.y; wd[2] = q.z; wd[3] = q.w;
-        }
         DF a{0.f, 0.f}, lmx{-INFINITY, 0.f}, lmn{INFINITY, 0.f};
         int lsx = INT_MAX, lsn = INT_MAX;
         if (have) {
@@ -238,29 +241,44 @@ static __device__ Candidate rescan_feature(const JobDesc &J, int32_t f, RunResul
     __syncthreads();
     Candidate cd;
     cd.err_hi = INFINITY; cd.err_lo = 0.f; cd.feature = f; cd.split = 0; cd.polarity = 1; cd.pad = 0;
-    if (threadIdx.x == 0) {
-        const DF Tp = df_from_double(J.rs->t_pos), Tm = df_from_double(J.rs->t_neg);
-        DF offs{0.f, 0.f}, bmax{0.f, 0.f}, bmn{0.f, 0.f};  // split 0: D = 0
-        int smax = 0, smn = 0;
-        for (int k = 0; k < 32; ++k) {  // runs in value order
-            const RunResult &q = rres[k];
-            if (q.smx != INT_MAX) {
-                const DF cc = df_add(offs, q.mx);
-                if (df_less(bmax, cc)) { bmax = cc; smax = q.smx; }
-            }
-            if (q.smn != INT_MAX) {
-                const DF cc = df_add(offs, q.mn);
-                if (df_less(cc, bmn)) { bmn = cc; smn = q.smn; }
-            }
-            offs = df_add(offs, q.total);
+    if (warp == 0) {
+        // runs in value order: an exclusive double-float scan of their totals
+        // places each run's extremes in the row; then the largest and the
+        // smallest prefix over the row (lowest split on ties), split 0 (D = 0)
+        // included
+        const RunResult q = rres[lane];
+        DF x = q.total;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const DF y = df_shfl_up(x, d);
+            if (lane >= d) x = df_add(y, x);
         }
-        const DF ep = df_add(Tp, df_neg(bmax));
-        const DF em = df_add(Tm, bmn);
-        const bool minus = df_less(em, ep) || (df_eq(em, ep) && smn < smax);
-        cd.err_hi = minus ? em.hi : ep.hi;
-        cd.err_lo = minus ? em.lo : ep.lo;
-        cd.split = minus ? smn : smax;
-        cd.polarity = minus ? -1 : 1;
+        DF offs = df_shfl_up(x, 1);
+        if (lane == 0) offs = DF{0.f, 0.f};
+        DF bmax = q.smx != INT_MAX ? df_add(offs, q.mx) : DF{-INFINITY, 0.f};
+        DF bmn = q.smn != INT_MAX ? df_add(offs, q.mn) : DF{INFINITY, 0.f};
+        int smax = q.smx, smn = q.smn;
+#pragma unroll
+        for (int d = 16; d; d >>= 1) {
+            const DF om = df_shfl_xor(bmax, d);
+            const int os = __shfl_xor_sync(0xffffffffu, smax, d);
+            if (df_less(bmax, om) || (df_eq(om, bmax) && os < smax)) { bmax = om; smax = os; }
+            const DF on = df_shfl_xor(bmn, d);
+            const int on_s = __shfl_xor_sync(0xffffffffu, smn, d);
+            if (df_less(on, bmn) || (df_eq(on, bmn) && on_s < smn)) { bmn = on; smn = on_s; }
+        }
+        if (!df_less(DF{0.f, 0.f}, bmax)) { bmax = DF{0.f, 0.f}; smax = 0; }
+        if (!df_less(bmn, DF{0.f, 0.f})) { bmn = DF{0.f, 0.f}; smn = 0; }
+        if (lane == 0) {
+            const DF Tp = df_from_double(J.rs->t_pos), Tm = df_from_double(J.rs->t_neg);
+            const DF ep = df_add(Tp, df_neg(bmax));
+            const DF em = df_add(Tm, bmn);
+            const bool minus = df_less(em, ep) || (df_eq(em, ep) && smn < smax);
+            cd.err_hi = minus ? em.hi : ep.hi;
+            cd.err_lo = minus ? em.lo : ep.lo;
+            cd.split = minus ? smn : smax;
+            cd.polarity = minus ? -1 : 1;
+        }
     }
     __syncthreads();
     return cd;
@@ -286,9 +304,15 @@ static __device__ void select_stump(const JobDesc &J, int cnt) {
     }
     if (lane == 0) wc[warp] = b;
     __syncthreads();
+    if (warp == 0) {
+        b = wc[lane];  // kRescanWarps == 32
+#pragma unroll
+        for (int d = 16; d; d >>= 1) {
+            const Candidate o = cand_shfl_xor(b, d);
+            if (cand_less(o, b)) b = o;
+        }
+    }
     if (threadIdx.x == 0) {
-        for (int w = 1; w < kRescanWarps; ++w)
-            if (cand_less(wc[w], b)) b = wc[w];
         RoundState *rs = J.rs;
         if (cnt == 0 || b.feature == INT_MAX) {
             rs->flags |= kFlagNoCandidate;

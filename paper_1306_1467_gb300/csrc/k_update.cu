@@ -189,33 +189,45 @@ __device__ __forceinline__ void sum_partials(const double *partials, int nblocks
     for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += red[0][k]; b += red[1][k]; c += red[2][k]; }
 }
 
+// The searched stump's canonical threshold: p=+1 -> value at position s
+// (max+1 at s = n); p=-1 -> value at position s-1 (min-1 at s = 0).  One
+// thread of the update's first block stores it in the round state before
+// that block is counted, off the finishing block's path.
+__device__ void store_threshold(const JobDesc &J) {
+    RoundState *rs = J.rs;
+    if (rs->forced) return;
+    const int n = J.lay.n;
+    const int32_t f = rs->win_feature, p = rs->win_polarity, s = rs->win_split;
+    const DevFeature d = J.feat[f];
+    const uint16_t *row = J.rows + (size_t)f * J.npad;
+    auto val_at = [&](int pos) {
+        const int P = phys_of(pos, J.npad / 32);
+        const int i = word_to_sample(entry_word(row[P], P), J.lay);
+        return haar_value(J.ii, J.ii_stride, J.win_w, d.type, d.x, d.y, d.w, d.h, i);
+    };
+    int32_t theta;
+    if (p > 0) theta = (s < n) ? val_at(s) : val_at(n - 1) + 1;
+    else theta = (s > 0) ? val_at(s - 1) : val_at(0) - 1;
+    rs->win_theta = theta;
+}
+
 // Step 3-4, part 1, finish (thread 0, after every block; the CTA's threads
 // have summed the partials): the stump's FP64 error, threshold, beta and
 // alpha, its record, and the update factors.
 __device__ void update_a_finish(const JobDesc &J, double M, double T, double B) {
     RoundState *rs = J.rs;
-    const int n = J.lay.n;
     const bool forced = rs->forced != 0;
     const int32_t f = forced ? rs->forced_feature : rs->win_feature;
     const int32_t p = forced ? rs->forced_polarity : rs->win_polarity;
     const int32_t s = forced ? 0 : rs->win_split;
-    const DevFeature d = J.feat[f];
     const double eps = M / T;
     int32_t theta, split = s;
     if (forced) {
         theta = rs->forced_threshold;
         split = (int32_t)B;
     } else {
-        // canonical threshold: p=+1 -> value at position s (max+1 at s = n);
-        // p=-1 -> value at position s-1 (min-1 at s = 0)
-        const uint16_t *row = J.rows + (size_t)f * J.npad;
-        auto val_at = [&](int pos) {
-            const int P = phys_of(pos, J.npad / 32);
-            const int i = word_to_sample(entry_word(row[P], P), J.lay);
-            return haar_value(J.ii, J.ii_stride, J.win_w, d.type, d.x, d.y, d.w, d.h, i);
-        };
-        if (p > 0) theta = (s < n) ? val_at(s) : val_at(n - 1) + 1;
-        else theta = (s > 0) ? val_at(s - 1) : val_at(0) - 1;
+        // written by another CTA in this launch: read past this SM's L1
+        theta = *reinterpret_cast<volatile int32_t *>(&rs->win_theta);
     }
     vjb_stump st;
     st.feature = f;
@@ -301,6 +313,7 @@ __device__ void finish_b(const JobDesc &J, int nblocks) {
 __global__ void __launch_bounds__(kUpdateThreads) k_update_a(const JobDesc J) {
     if (J.rs->status != VJB_OK) return;
     update_a_block(J, blockIdx.x);
+    if (blockIdx.x == 0 && threadIdx.x == 0) store_threshold(J);
     if (!last_block_done(&J.rs->done_update_a, gridDim.x)) return;
     finish_a(J, gridDim.x);
 }
@@ -344,8 +357,12 @@ __global__ void __launch_bounds__(kUpdateThreads) k_bupdate(const JobDesc *__res
         const JobDesc &J = jobs[lo];
         const int blk = g - base[lo], nblocks = base[lo + 1] - base[lo];
         if (!J.rs->in_round || J.rs->status != VJB_OK) continue;
-        if (A) update_a_block(J, blk);
-        else update_b_block(J, blk);
+        if (A) {
+            update_a_block(J, blk);
+            if (blk == 0 && threadIdx.x == 0) store_threshold(J);
+        } else {
+            update_b_block(J, blk);
+        }
         if (last_block_done(A ? &J.rs->done_update_a : &J.rs->done_update_b, nblocks)) {
             if (A) finish_a(J, nblocks);
             else finish_b(J, nblocks);

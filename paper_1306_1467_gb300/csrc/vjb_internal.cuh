@@ -62,6 +62,7 @@ struct RoundState {
     float win_err_hi, win_err_lo;  // the stump's error from the compensated re-scan
     uint32_t screen_min_bits;  // batched search: smallest screened error (bits of a float >= 0)
     int32_t in_round;          // batched rounds: 1 if the job takes part in the current round
+    int32_t win_theta;         // the searched stump's threshold (set by the update's first block)
 };
 
 // Device error flags.
