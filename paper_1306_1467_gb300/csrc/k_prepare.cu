@@ -90,6 +90,19 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
     return m;
 }
 
+// End of a row's write (all threads of the CTA): count the row and flag an
+// entry before position n whose word lies outside the weight array or is the
+// padding word.  The search kernels gather weights through the table without
+// bounds checks; the host accepts a table only if no entry was flagged and
+// every row was counted.  stat[0]: kFlagBadTable or 0, stat[1]: rows written.
+__device__ __forceinline__ void row_written(bool bad, int32_t *stat) {
+    const int any_bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0) {
+        if (any_bad) atomicOr(&stat[0], kFlagBadTable);
+        atomicAdd(&stat[1], 1);
+    }
+}
+
 // Lanes of the warp holding the same BITS-bit digit `d` as this lane: one
 // ballot per digit bit, each narrowing the set to the lanes that agree on that
 // bit.  On this GPU BITS ballots (four instructions a bit) rank a sort pass
@@ -145,7 +158,7 @@ template <int IPT>
 __global__ void __launch_bounds__(kSortThreads, 1)
     k_sort_rows(const int32_t *__restrict__ ii_t, int ii_stride, int w,
                 const DevFeature *__restrict__ feat, int64_t f0, WeightLayout L,
-                uint16_t *__restrict__ rows, int npad, const int32_t *__restrict__ row_list) {
+                uint16_t *__restrict__ rows, int npad, const int32_t *__restrict__ row_list, int32_t *stat) {
     const int row = row_list ? row_list[blockIdx.x] : (int)blockIdx.x;  // row of the tile
     constexpr int NP = kSortThreads * IPT;
     const int n = L.n;
@@ -321,6 +334,7 @@ __global__ void __launch_bounds__(kSortThreads, 1)
             gchoice[g] = mask;
         }
         __syncthreads();
+        bool bad = false;
         for (int P = threadIdx.x; P < npad; P += kSortThreads) {
             const int p = logical_of(P, run);
             uint16_t e;
@@ -329,66 +343,30 @@ __global__ void __launch_bounds__(kSortThreads, 1)
                 int word = (int)(x & 0x7fffu);
                 const int k = (P >> 3) & 31, g = (P >> 8) * kChunkElems + (P & 7);  // p = k * run + g
                 if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
+                bad |= word >= L.words || word == n;
                 e = make_entry(word, (x & 0x8000u) != 0, P);
             } else {
                 e = make_entry(n, false, P);
             }
             out[P] = e;
         }
+        row_written(bad, stat);
         return;
     }
+    bool bad = false;
     for (int P = threadIdx.x; P < npad; P += kSortThreads) {
         const int p = logical_of(P, run);
         uint16_t e;
         if (p < n) {
             const bool step = (p == n - 1) || (skey[p] < skey[p + 1]);
+            bad |= (int)sidx[p] >= L.words || (int)sidx[p] == n;
             e = make_entry(sidx[p], step, P);
         } else {
             e = make_entry(n, false, P);
         }
         out[P] = e;
     }
-}
-
-// Validation of a finished table: every entry before position n names a word
-// inside the weight array other than the padding word, every entry from n on
-// is the padding entry (word n, no flag).  Sets kFlagBadTable in `flags` otherwise.  The search
-// kernels rely on this to gather weights without bounds checks.  One CTA per
-// row at a time, one 16-byte chunk (8 entries) per thread.
-__global__ void k_check_rows(const uint16_t *__restrict__ rows, int64_t nfeat, WeightLayout L,
-                             int npad, int32_t *flags) {
-    bool bad = false;
-    const int n = L.n, run = npad / 32, nch = npad / kChunkElems;
-    const uint32_t words = (uint32_t)L.words, pad = (uint32_t)n;
-    for (int64_t f = blockIdx.x; f < nfeat; f += gridDim.x) {
-        const uint4 *row = reinterpret_cast<const uint4 *>(rows + (size_t)f * npad);
-        for (int c = threadIdx.x; c < nch; c += blockDim.x) {
-            const uint4 q = __ldg(row + c);
-            const int p0 = (c & 31) * run + (c >> 5) * kChunkElems;  // logical position of entry 0
-            const uint32_t wd[4] = {q.x, q.y, q.z, q.w};
-            if (p0 + kChunkElems <= n) {
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t a = wd[j] & kIndexMask, b = wd[j] >> 17;
-                    bad |= a >= words || a == pad || b >= words || b == pad;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const uint32_t e = (j & 1) ? (wd[j >> 1] >> 16) : (wd[j >> 1] & 0xffffu);
-                    const uint32_t word = (uint32_t)entry_word(e, j);
-                    bad |= (p0 + j < n) ? (word >= words || word == pad) : (e != make_entry(n, false, j));
-                }
-            }
-        }
-    }
-    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flags, kFlagBadTable);
-}
-
-cudaError_t launch_check_rows(const uint16_t *rows, int64_t nfeat, const WeightLayout &L, int npad,
-                              int32_t *flags, int grid, cudaStream_t st) {
-    k_check_rows<<<grid, 256, 0, st>>>(rows, nfeat, L, npad, flags);
-    return cudaGetLastError();
+    row_written(bad, stat);
 }
 
 template <int IPT>
@@ -401,13 +379,13 @@ static size_t sort_smem() {
 template <int IPT>
 static cudaError_t launch_sort_ipt(const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
                                    int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows,
-                                   int npad, const int32_t *row_list, cudaStream_t st) {
+                                   int npad, const int32_t *row_list, int32_t *stat, cudaStream_t st) {
     const size_t sm = sort_smem<IPT>();
     cudaError_t e = cudaFuncSetAttribute(k_sort_rows<IPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)sm);
     if (e != cudaSuccess) return e;
     k_sort_rows<IPT><<<(unsigned)nf, kSortThreads, sm, st>>>(ii_t, ii_stride, w, feat, f0, L, rows, npad,
-                                                            row_list);
+                                                            row_list, stat);
     return cudaGetLastError();
 }
 
@@ -434,7 +412,7 @@ template <int IPT, int TH>
 __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
     k_sort_rows_packed(const int32_t *__restrict__ ii_t, int ii_stride, int w,
                        const DevFeature *__restrict__ feat, int64_t f0, WeightLayout L,
-                       uint16_t *__restrict__ rows, int npad, int32_t *ovf) {
+                       uint16_t *__restrict__ rows, int npad, int32_t *ovf, int32_t *stat) {
     constexpr int NP = TH * IPT;
     constexpr int WARPS = TH / 32, HSTRIDE = WARPS + 1, HWORDS = kPkRadix * HSTRIDE;
     constexpr int GROUPS = NP / 32;  // lane-run groups of the longest row
@@ -674,6 +652,7 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
         }
         __syncthreads();
     }
+    bool bad = false;
     for (int P = threadIdx.x; P < npad; P += TH) {
         const int p = logical_of(P, run);
         uint16_t e;
@@ -685,12 +664,14 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
                 const int k = (P >> 3) & 31, g = (P >> 8) * kChunkElems + (P & 7);
                 if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
             }
+            bad |= word >= L.words || word == n;
             e = make_entry(word, step, P);
         } else {
             e = make_entry(n, false, P);
         }
         out[P] = e;
     }
+    row_written(bad, stat);
 }
 
 template <int IPT, int TH>
@@ -704,21 +685,22 @@ static size_t sort_packed_smem() {
 template <int IPT, int TH = kPkThreads>
 static cudaError_t launch_sort_packed(const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
                                       int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows,
-                                      int npad, int32_t *ovf, cudaStream_t st) {
+                                      int npad, int32_t *ovf, int32_t *stat, cudaStream_t st) {
     const size_t sm = sort_packed_smem<IPT, TH>();
     cudaError_t e = cudaFuncSetAttribute(k_sort_rows_packed<IPT, TH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_sort_rows_packed<IPT, TH><<<(unsigned)nf, TH, sm, st>>>(ii_t, ii_stride, w, feat, f0, L, rows, npad, ovf);
+    k_sort_rows_packed<IPT, TH><<<(unsigned)nf, TH, sm, st>>>(ii_t, ii_stride, w, feat, f0, L, rows, npad, ovf,
+                                                              stat);
     return cudaGetLastError();
 }
 
 // Two-word sort of `nf` rows of the tile (all of them, or those listed).
 static cudaError_t launch_sort_wide(const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
                                    int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows, int npad,
-                                   const int32_t *row_list, cudaStream_t st) {
+                                   const int32_t *row_list, int32_t *stat, cudaStream_t st) {
     const int n = L.n;
-#define VJB_SORT_CASE(I) launch_sort_ipt<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, row_list, st)
+#define VJB_SORT_CASE(I) launch_sort_ipt<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, row_list, stat, st)
     if (n <= kSortThreads * 1) return VJB_SORT_CASE(1);
     if (n <= kSortThreads * 2) return VJB_SORT_CASE(2);
     if (n <= kSortThreads * 4) return VJB_SORT_CASE(4);
@@ -730,19 +712,22 @@ static cudaError_t launch_sort_wide(const int32_t *ii_t, int ii_stride, int w, c
 
 // Rows of a tile: the packed sort for every row (512 threads up to 16,384
 // samples, 1024 above), then the two-word sort for the rows whose value span
-// and sample index do not fit one word, which the packed sort lists in ovf
-// (count, then rows; 1 + nf ints of device memory).  Waits for the stream
-// when it reads the count.
+// and sample index do not fit one word, which the packed sort lists.
+// `scratch` (3 + nf ints of device memory): [0] and [1] the table's check
+// state (see row_written; zeroed by the caller once per table), [2] the
+// tile's listed-row count, then the listed rows.  Waits for the stream when
+// it reads the count.
 cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, const DevFeature *feat,
                              int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows, int npad,
-                             int32_t *ovf, cudaStream_t st) {
+                             int32_t *scratch, cudaStream_t st) {
     (void)h;
     if (nf <= 0) return cudaSuccess;
     const int n = L.n;
+    int32_t *stat = scratch, *ovf = scratch + 2;
     cudaError_t e = cudaMemsetAsync(ovf, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     if (n <= kPkThreads * 32) {
-#define VJB_PK_CASE(I) launch_sort_packed<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, ovf, st)
+#define VJB_PK_CASE(I) launch_sort_packed<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, ovf, stat, st)
         const int ipt = (n + kPkThreads - 1) / kPkThreads;
         if (ipt <= 4) e = VJB_PK_CASE(4);
         else if (ipt <= 8) e = VJB_PK_CASE(8);
@@ -755,7 +740,8 @@ cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, c
         else e = VJB_PK_CASE(32);
 #undef VJB_PK_CASE
     } else {
-#define VJB_PK_WIDE(I) launch_sort_packed<I, 1024>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, ovf, st)
+#define VJB_PK_WIDE(I) \
+    launch_sort_packed<I, 1024>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, ovf, stat, st)
         const int ipt = (n + 1023) / 1024;
         if (ipt <= 20) e = VJB_PK_WIDE(20);
         else if (ipt <= 24) e = VJB_PK_WIDE(24);
@@ -768,7 +754,7 @@ cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, c
     e = cudaMemcpyAsync(&count, ovf, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess || count == 0) return e;
-    return launch_sort_wide(ii_t, ii_stride, w, feat, f0, count, L, rows, npad, ovf + 1, st);
+    return launch_sort_wide(ii_t, ii_stride, w, feat, f0, count, L, rows, npad, ovf + 1, stat, st);
 }
 
 }  // namespace vjb

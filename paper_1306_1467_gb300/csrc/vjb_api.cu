@@ -372,25 +372,29 @@ int prepare_tables(vjb_ctx *c) {
         if (c->rows_external) return fail(VJB_ESTATE, "external table not set");
         CK(cudaMalloc(&c->d_rows, sizeof(uint16_t) * (size_t)c->nfeat * c->npad));
     }
-    // feature values (the K2 arithmetic, fused into the sort) and sort, a tile of rows per launch
+    // feature values (the K2 arithmetic, fused into the sort) and sort, a tile
+    // of rows per launch; the sort kernels check every entry they write (the
+    // search kernels gather through the table without bounds checks) and
+    // count the rows they write
     const int64_t tile = std::max<int64_t>(1, std::min<int64_t>(c->nfeat, 65535));
-    int32_t *d_ovf = nullptr;  // rows the packed sort hands to the two-word sort
-    CK(cudaMalloc(&d_ovf, sizeof(int32_t) * (size_t)(1 + tile)));
-    for (int64_t f0 = 0; f0 < c->nfeat; f0 += tile) {
+    // (kept with the context: a cudaFree here would wait for the whole device,
+    // other contexts' rounds included, when a server prepares a request)
+    if (!c->d_scratch) CK(cudaMalloc(&c->d_scratch, sizeof(int32_t) * (size_t)(3 + tile)));
+    int32_t *d_scratch = c->d_scratch;  // check state, then the rows the packed sort hands to the two-word sort
+    cudaError_t e = cudaMemsetAsync(d_scratch, 0, 2 * sizeof(int32_t), c->stream);
+    for (int64_t f0 = 0; f0 < c->nfeat && e == cudaSuccess; f0 += tile) {
         const int64_t nf = std::min(tile, c->nfeat - f0);
-        const cudaError_t e = launch_sort_rows(c->d_ii, c->ii_stride, c->w, c->h, c->d_feat, f0, nf, c->lay,
-                                               c->d_rows + (size_t)f0 * c->npad, c->npad, d_ovf, c->stream);
-        if (e != cudaSuccess) {
-            cudaFree(d_ovf);
-            return fail(VJB_ECUDA, "sort of rows %lld..: %s", (long long)f0, cudaGetErrorString(e));
-        }
+        e = launch_sort_rows(c->d_ii, c->ii_stride, c->w, c->h, c->d_feat, f0, nf, c->lay,
+                             c->d_rows + (size_t)f0 * c->npad, c->npad, d_scratch, c->stream);
         c->launches += 1;
     }
-    CK(cudaStreamSynchronize(c->stream));
-    dfree(d_ovf);
-    // the search kernels gather through the table without bounds checks: validate it once
-    CK(launch_check_rows(c->d_rows, c->nfeat, c->lay, c->npad, flags_ptr(c), c->num_sms * 8, c->stream));
-    c->launches += 1;
+    int32_t stat[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stat, d_scratch, sizeof stat, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return fail(VJB_ECUDA, "sort of the feature rows: %s", cudaGetErrorString(e));
+    if (stat[0] || stat[1] != c->nfeat)
+        return fail(VJB_EDEVICE, "sorted table check failed: flags 0x%x, %d of %lld rows written", stat[0],
+                    stat[1], (long long)c->nfeat);
     RoundState rs;
     int rc = read_state(c, &rs);
     if (rc) return rc;

@@ -95,6 +95,7 @@ struct vjb_ctx {
     Candidate *d_cand = nullptr;
     int32_t *d_cand_ids = nullptr;
     uint8_t *d_miss = nullptr;
+    int32_t *d_scratch = nullptr;  // table preparation: check state and listed rows
     double *d_partials = nullptr;
     RoundState *d_rs = nullptr;
     vjb_stump *d_stumps = nullptr, *d_last = nullptr;
@@ -135,7 +136,7 @@ struct vjb_ctx {
         dfree(d_rows);
         rows_external = false;
         dfree(d_w); dfree(d_v); dfree(d_wtmp); dfree(d_ferr); dfree(d_bmin); dfree(d_cand);
-        dfree(d_cand_ids); dfree(d_miss); dfree(d_partials);
+        dfree(d_cand_ids); dfree(d_miss); dfree(d_partials); dfree(d_scratch);
         dfree(d_rs); dfree(d_stumps); dfree(d_last); dfree(d_diag);
         stump_cap = bmin_cap = 0;
         feats.clear();

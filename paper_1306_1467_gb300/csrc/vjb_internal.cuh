@@ -208,9 +208,7 @@ cudaError_t launch_feature_values(const int32_t *ii_t, int ii_stride, int n, int
                                   cudaStream_t st);
 cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, const DevFeature *feat,
                              int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows, int npad,
-                             int32_t *ovf, cudaStream_t st);
-cudaError_t launch_check_rows(const uint16_t *rows, int64_t nfeat, const WeightLayout &L, int npad,
-                              int32_t *flags, int grid, cudaStream_t st);
+                             int32_t *scratch, cudaStream_t st);
 cudaError_t launch_init_weights(const uint8_t *y, const WeightLayout &L, const float *w_in,
                                 float *w, float *v, RoundState *rs, cudaStream_t st);
 cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, const WeightLayout &L,

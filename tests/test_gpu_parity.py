@@ -439,3 +439,60 @@ def test_rows_too_wide_for_one_word_take_the_two_word_sort():
         assert np.array_equal(feats, desc)
         for k, f in enumerate(picks):
             _check_rows(tr.sorted_rows(f, 1), vals[k:k + 1], order[k:k + 1])
+
+
+@pytest.mark.parametrize("hi", [0, 1, 3, 15, 255])
+def test_sort_every_digit_width(hi):
+    """The sort takes one pass when a row's value span has at most 9 bits and
+    two over half the span's bits (5 to 9) otherwise.  Pixels drawn from
+    [0, hi] on 8x8 windows give spans from 0 bits (hi = 0: every value ties)
+    to 13 (two passes of 5, 6 and 7 bits; 24x24 rows reach 8-bit digits and
+    the 18-bit test below 9); 15,000 windows run the 512-thread packed sort
+    with 30 items per thread, as at 24x24 / 15k.  Every row bit for bit
+    against the oracle's stable order, and the spans seen cover the widths in
+    question."""
+    rng = np.random.Generator(np.random.PCG64(700 + hi))
+    n = 15000
+    px = rng.integers(0, hi + 1, size=(n, 8, 8), dtype=np.uint8)
+    y = (rng.random(n) < 0.4).astype(np.uint8)
+    desc, _ = O.haar_enumerate(8, 8)
+    vals = O.feature_values(px, desc)
+    order = O.sort_rows(vals)
+    span = vals.max(axis=1).astype(np.int64) - vals.min(axis=1)
+    bits = np.where(span > 0, np.floor(np.log2(np.maximum(span, 1))).astype(int) + 1, 0)
+    with _trainer() as tr:
+        assert np.array_equal(tr.prepare(px, y), desc)
+        _check_rows(tr.sorted_rows(0, desc.shape[0]), vals, order)
+    seen = set(bits.tolist())
+    want = {0: {0}, 1: {2, 3, 4, 5, 6}, 3: {3, 4, 5, 6, 7}, 15: {5, 6, 7, 8, 9}, 255: {10, 11, 12, 13}}[hi]
+    assert want <= seen, (hi, sorted(seen))
+
+
+def test_sort_18_bit_spans_packed():
+    """Below 16,385 windows a packed item has a 14-bit index, so a value span
+    of up to 18 bits still sorts in one word: two 9-bit passes.  Windows half
+    black / half white (and the inverse) give the full-window two-rectangle
+    features a span of 146,880 (18 bits); those rows and a few ordinary ones
+    bit for bit against the oracle's stable order."""
+    from paper_1306_1467_gb300 import vjb
+    rng = np.random.Generator(np.random.PCG64(6))
+    n = 3000
+    px = rng.integers(100, 156, size=(n, 24, 24), dtype=np.uint8)
+    half = rng.random(n) < 0.5
+    px[half, :, :12] = 0
+    px[half, :, 12:] = 255
+    px[~half, :, :12] = 255
+    px[~half, :, 12:] = 0
+    y = (rng.random(n) < 0.4).astype(np.uint8)
+    desc, _ = O.haar_enumerate(24, 24)
+    wide = int(np.flatnonzero((desc[:, 0] == vjb.HAAR_TYPES.index("2H")) & (desc[:, 1] == 0) &
+                              (desc[:, 2] == 0) & (desc[:, 3] == 24) & (desc[:, 4] == 24))[0])
+    picks = [wide, 0, 1000, 50000, 120000, desc.shape[0] - 1]
+    vals = O.feature_values(px, desc[picks])
+    span = vals.max(axis=1).astype(np.int64) - vals.min(axis=1)
+    assert span[0] >= 1 << 17
+    order = O.sort_rows(vals)
+    with _trainer() as tr:
+        tr.prepare(px, y)
+        for k, f in enumerate(picks):
+            _check_rows(tr.sorted_rows(f, 1), vals[k:k + 1], order[k:k + 1])
