@@ -17,9 +17,9 @@
 //    A warp scans one row: lane k walks its own run of the value order (the
 //    row layout interleaves 32 runs), summing 16 or 24 entries at a time in
 //    FP32 and folding each piece into a compensated (TwoSum) running total; one
-//    double-float warp scan of the 32 run totals per row places every lane's
-//    best prefix in the row.  It writes each feature's FP32 error and each
-//    CTA's minimum.
+//    FP32 warp scan of the 32 run totals per row places every lane's best
+//    prefix in the row.  It writes each feature's FP32 error and each CTA's
+//    minimum.
 //  * k_shortlist: lists every feature whose screened error is within a margin
 //    of the smallest one.
 //  * k_rescan: one CTA per listed feature scans its row again in double-float
@@ -29,10 +29,12 @@
 //
 // Screening error bound (u = 2^-24, sum |v| = T+ + T- = 1 after normalising):
 // a piece's partial sums of at most 24 terms err by at most 24u times the
-// piece's |v| mass; the compensated run total and the double-float scan of run
-// totals add O(u^2); placing the piece's extreme on the run total, and that on
-// the run offset, adds 4u |D|; forming T+- -/+ D in FP32 adds 2u.  So
-// |screened - exact| <= 30u.  A margin of 64u (twice 32u) keeps every
+// piece's |v| mass; the compensated run total adds O(u^2); placing the
+// piece's extreme on the run total adds 2u |D|; rounding the 32 run totals
+// to FP32 adds u, their five-level FP32 scan 5u (each total passes through
+// at most five additions, sum |run totals| <= 1), and placing a lane's
+// extreme on its run offset u |D|; forming T+- -/+ D in FP32 adds 2u.  So
+// |screened - exact| <= 35u.  A margin of 72u (twice 36u) keeps every
 // feature that could beat the best one.
 #include <limits.h>
 #include <math.h>

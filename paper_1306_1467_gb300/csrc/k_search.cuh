@@ -99,20 +99,23 @@ __device__ __forceinline__ void scan_stage(uint32_t sbase, int crs, int lane, co
 }
 
 // End of a row: the runs of the lanes below come first, so an exclusive
-// double-float scan of the run totals offsets each lane's best prefixes; the
-// feature's error is min(T+ - max D, T- + min D), split 0 (D = 0) included.
+// scan of the run totals offsets each lane's best prefixes; the feature's
+// error is min(T+ - max D, T- + min D), split 0 (D = 0) included.  The scan is
+// plain FP32 over the run totals rounded once (it adds at most 6u of the
+// weight total to the screening bound of k_search.cu; a double-float scan
+// here cost about 2% of the search at 15,000 samples and 13% at 2,500).
 __device__ __forceinline__ float finish_row(float ahi, float alo, float bmx, float bmn, float Tp,
                                             float Tm, int lane) {
-    DF x{ahi, alo};
+    float x = ahi + alo;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-        const DF y = df_shfl_up(x, d);
-        if (lane >= d) x = df_add(y, x);
+        const float y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
     }
-    DF excl = df_shfl_up(x, 1);
-    if (lane == 0) excl = DF{0.f, 0.f};
-    float MX = warp_max(excl.hi + (excl.lo + bmx));
-    float MN = warp_min(excl.hi + (excl.lo + bmn));
+    float excl = __shfl_up_sync(0xffffffffu, x, 1);
+    if (lane == 0) excl = 0.f;
+    float MX = warp_max(excl + bmx);
+    float MN = warp_min(excl + bmn);
     MX = fmaxf(MX, 0.f);
     MN = fminf(MN, 0.f);
     return fminf(Tp - MX, Tm + MN);

@@ -124,7 +124,7 @@ __host__ __device__ __forceinline__ bool entry_flag(uint32_t e, int phys) {
 // Margin (in units of 2^-24 times the weight total) within which a feature's
 // FP32 screened error must lie of the smallest one to be re-scanned
 // compensated.  It is twice a bound on the screening error (see k_search.cu).
-constexpr float kScreenMarginUlps = 64.0f;
+constexpr float kScreenMarginUlps = 72.0f;
 
 // Partials of the multi-CTA update kernels (one slot per CTA).
 constexpr int kUpdateThreads = 256;

@@ -3,8 +3,8 @@
 Bars (from the method's definition):
   * integral images, feature values, sorted sample orders and their tie
     flags: bit-exact;
-  * per-feature FP32 screened errors: within 32 * 2^-24 of the oracle's FP64
-    per-feature minimum (the screening bound is 26 * 2^-24 times the weight
+  * per-feature FP32 screened errors: within 36 * 2^-24 of the oracle's FP64
+    per-feature minimum (the screening bound is 35 * 2^-24 times the weight
     total, see k_search.cu);
   * each round, on the same FP32 weights: the chosen (feature, threshold,
     polarity) equals the oracle's unless the oracle's two best errors lie
@@ -23,7 +23,7 @@ from paper_1306_1467_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 REL = 1e-6
-SCREEN_TOL = 32 * 2.0 ** -24
+SCREEN_TOL = 36 * 2.0 ** -24
 
 
 def _trainer():
