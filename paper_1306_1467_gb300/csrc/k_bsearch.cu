@@ -165,8 +165,12 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
                     ok = false;
                     break;
                 }
-                const int lh = min(stage_lines, lines - c * stage_lines);
-                scan_stage<U>(ring_w + (uint32_t)cstage * stage_bytes, lh >> 2, lane, sv, ahi, alo, bmx, bmn);
+                const uint32_t sbase = ring_w + (uint32_t)cstage * stage_bytes;
+                if (U == 3 && stage_lines == 24 && c != nc - 1)  // full stages of the default shape
+                    scan_pieces<2, 3>(sbase, 0, lane, sv, ahi, alo, bmx, bmn);
+                else
+                    scan_stage<U>(sbase, min(stage_lines, lines - c * stage_lines) >> 2, lane, sv, ahi, alo,
+                                  bmx, bmn);
                 __syncwarp();
                 if (lane == 0) {
                     fence_proxy_async_smem();
@@ -326,8 +330,12 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
                     ok = false;
                     break;
                 }
-                const int lh = min(stage_lines, lines - c * stage_lines);
-                scan_stage<U>(ring_w + (uint32_t)cstage * stage_bytes, lh >> 2, lane, sv, ahi, alo, bmx, bmn);
+                const uint32_t sbase = ring_w + (uint32_t)cstage * stage_bytes;
+                if (U == 3 && stage_lines == 24 && c != nc - 1)  // full stages of the default shape
+                    scan_pieces<2, 3>(sbase, 0, lane, sv, ahi, alo, bmx, bmn);
+                else
+                    scan_stage<U>(sbase, min(stage_lines, lines - c * stage_lines) >> 2, lane, sv, ahi, alo,
+                                  bmx, bmn);
                 __syncwarp();
                 if (lane == 0) {
                     fence_proxy_async_smem();
@@ -466,8 +474,12 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
                     ok = false;
                     break;
                 }
-                const int lh = min(stage_lines, lines - c * stage_lines);
-                scan_stage<U>(ring_w + (uint32_t)cstage * stage_bytes, lh >> 2, lane, sv, ahi, alo, bmx, bmn);
+                const uint32_t sbase = ring_w + (uint32_t)cstage * stage_bytes;
+                if (U == 3 && stage_lines == 24 && c != nc - 1)  // full stages of the default shape
+                    scan_pieces<2, 3>(sbase, 0, lane, sv, ahi, alo, bmx, bmn);
+                else
+                    scan_stage<U>(sbase, min(stage_lines, lines - c * stage_lines) >> 2, lane, sv, ahi, alo,
+                                  bmx, bmn);
                 __syncwarp();
                 if (lane == 0) {
                     fence_proxy_async_smem();

@@ -84,10 +84,17 @@ __device__ __forceinline__ void scan_pieces(uint32_t sbase, int t0, int lane, co
 
 // All chunk rows of one stage, 2U chunk rows (16U entries per lane) at a
 // time: U pieces of 16 entries, or with U = 3 two pieces of 24 (fewer piece
-// ends to fold in; 24 terms keep the screening bound of k_search.cu).
+// ends to fold in; 24 terms keep the screening bound of k_search.cu).  A full
+// stage of 2U chunk rows -- all but a row's last stage -- takes a path of its
+// own with no loop around it (3.4% of the search time at 24x24 / 15k).
 template <int U>
 __device__ __forceinline__ void scan_stage(uint32_t sbase, int crs, int lane, const float *sv,
                                            float &ahi, float &alo, float &bmx, float &bmn) {
+    if (crs == 2 * U) {
+        if constexpr (U == 3) scan_pieces<2, 3>(sbase, 0, lane, sv, ahi, alo, bmx, bmn);
+        else scan_pieces<U, 2>(sbase, 0, lane, sv, ahi, alo, bmx, bmn);
+        return;
+    }
     int t = 0;
     if constexpr (U == 3) {
         for (; t + 6 <= crs; t += 6) scan_pieces<2, 3>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
