@@ -641,9 +641,9 @@ int vjb_batch_get_info(vjb_batch *b, vjb_batch_info *out) {
 // A server keeps one batch on the device.  Requests wait in arrival order
 // until their sorted table fits the free part of the batch's arena (and a job
 // slot is free); a worker thread then prepares each admitted request on its
-// own stream -- windows, integral images, features, sorted table written into
-// the arena -- while the main thread keeps running batched rounds for the jobs
-// already training.  A prepared request joins the batch at the next round;
+// low-priority stream -- windows, integral images, features, sorted table
+// written into the arena -- while the main thread keeps running batched
+// rounds for the jobs already training, on a high-priority stream.  A prepared request joins the batch at the next round;
 // a job that reaches its round count (or stops early) leaves it, its stumps
 // and weights are copied to the host and its table space is freed for the
 // requests still waiting.
@@ -687,7 +687,11 @@ struct vjb_server {
     std::condition_variable cv_work, cv_done;
     std::deque<ServerReq *> to_prepare;
     std::vector<ServerReq *> prepared;
+    std::vector<vjb_ctx *> to_destroy;  // retired jobs' contexts: their cudaFree waits for the device
     bool stop = false;
+    // rounds run on a high-priority stream, preparation on a low-priority one,
+    // so that a round's CTAs go ahead of a running sort's as SMs free up
+    cudaStream_t hi = nullptr, lo = nullptr;
     int preparing = 0;  // admitted, not yet collected (main thread only)
     std::vector<float> round_ms;
     std::vector<int32_t> round_jobs;
@@ -703,7 +707,7 @@ namespace {
 // Worker side: build a request's context with its table in the arena.
 int server_prepare(vjb_server *s, ServerReq *r) {
     vjb_ctx *c = nullptr;
-    int rc = vjb_create(&c, s->device, nullptr);
+    int rc = vjb_create(&c, s->device, s->lo);
     if (rc == VJB_OK) rc = vjb_load_windows(c, r->px.data(), r->y.data(), r->n, r->h, r->w);
     if (rc == VJB_OK) {
         c->rows_external = true;
@@ -727,12 +731,22 @@ void server_worker(vjb_server *s) {
     cudaSetDevice(s->device);
     for (;;) {
         ServerReq *r = nullptr;
+        std::vector<vjb_ctx *> dead;
         {
             std::unique_lock<std::mutex> lk(s->mu);
-            s->cv_work.wait(lk, [&] { return s->stop || !s->to_prepare.empty(); });
-            if (s->to_prepare.empty()) return;  // stop requested and nothing left
-            r = s->to_prepare.front();
-            s->to_prepare.pop_front();
+            s->cv_work.wait(lk, [&] { return s->stop || !s->to_prepare.empty() || !s->to_destroy.empty(); });
+            dead.swap(s->to_destroy);
+            if (!s->to_prepare.empty()) {
+                r = s->to_prepare.front();
+                s->to_prepare.pop_front();
+            }
+        }
+        // freeing device memory waits for the whole device: here, not on the
+        // thread that runs the rounds
+        for (vjb_ctx *c : dead) vjb_destroy(c);
+        if (!r) {
+            if (s->stop) return;  // stop requested and nothing left
+            continue;
         }
         const int rc = s->stop ? VJB_ESTATE : server_prepare(s, r);
         {
@@ -809,7 +823,11 @@ int server_retire(vjb_server *s, const std::vector<RoundState> &st) {
             r->px.clear();
             r->px.shrink_to_fit();
         }
-        vjb_destroy(sl.ctx);
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            s->to_destroy.push_back(sl.ctx);
+        }
+        s->cv_work.notify_all();
         arena_give(b, sl.line_base, sl.line_count);
         b->dirty = true;
     }
@@ -858,11 +876,29 @@ int vjb_server_create(vjb_server **out, int device, int64_t table_budget_bytes, 
     *out = nullptr;
     if (max_jobs < 1 || max_jobs > kMaxBatchJobs)
         return fail(VJB_EINVAL, "max_jobs = %d outside [1, %d]", max_jobs, kMaxBatchJobs);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(VJB_EINVAL, "device %d out of range", device);
+    CK(cudaSetDevice(device));
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    cudaStream_t hi = nullptr, lo = nullptr;
+    CK(cudaStreamCreateWithPriority(&hi, cudaStreamNonBlocking, greatest));
+    if (cudaStreamCreateWithPriority(&lo, cudaStreamNonBlocking, least) != cudaSuccess) {
+        cudaStreamDestroy(hi);
+        return fail(VJB_ECUDA, "stream creation failed");
+    }
     vjb_batch *b = nullptr;
-    int rc = vjb_batch_create(&b, device, nullptr, table_budget_bytes);
-    if (rc) return rc;
+    int rc = vjb_batch_create(&b, device, hi, table_budget_bytes);
+    if (rc) {
+        cudaStreamDestroy(hi);
+        cudaStreamDestroy(lo);
+        return rc;
+    }
     vjb_server *s = new vjb_server();
     s->b = b;
+    s->hi = hi;
+    s->lo = lo;
     s->device = device;
     s->max_jobs = max_jobs;
     s->t0 = std::chrono::steady_clock::now();
@@ -882,7 +918,10 @@ void vjb_server_destroy(vjb_server *s) {
     cudaSetDevice(s->device);
     for (ServerReq *r : s->prepared)
         if (r->ctx) vjb_destroy(r->ctx);
+    for (vjb_ctx *c : s->to_destroy) vjb_destroy(c);
     vjb_batch_destroy(s->b);  // destroys the contexts of the training jobs
+    cudaStreamDestroy(s->hi);
+    cudaStreamDestroy(s->lo);
     delete s;
 }
 
