@@ -584,67 +584,60 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
     const int run = npad / 32;
     if (L.dual) {
         // bank-balanced copy choice per gather group (see k_sort_rows); the
-        // loads of the 32 banks live in registers as 2-bit counters, banks
-        // 0-15 in cl and 16-31 in ch (a load above 3 counts as 3).  Only the
-        // groups left with a bank at 3 after the greedy pass get the pass of
-        // single moves; they are listed first (in the free histogram space) so
-        // that the threads share them evenly.
-        auto level = [](uint32_t cl, uint32_t ch, int b) { return ((b < 16 ? cl : ch) >> (2 * (b & 15))) & 3u; };
-        auto inc = [&](uint32_t &cl, uint32_t &ch, int b) {
-            if (level(cl, ch, b) == 3u) return;
-            const uint32_t one = 1u << (2 * (b & 15));
-            if (b < 16) cl += one;
-            else ch += one;
+        // loads of the 32 banks as 2-bit counters in one 64-bit word (bank b
+        // at bits 2b, 2b + 1; a load above 3 counts as 3).  Only the groups
+        // left with a bank at 3 after the greedy pass get the pass of single
+        // moves; they are listed first (in the free histogram space) so that
+        // the threads share them evenly.
+        auto level = [](uint64_t C, int b) { return (uint32_t)(C >> (2 * b)) & 3u; };
+        auto inc = [&](uint64_t &C, int b) {
+            if (level(C, b) != 3u) C += 1ull << (2 * b);
         };
-        auto dec = [&](uint32_t &cl, uint32_t &ch, int b) {
-            if (level(cl, ch, b) == 0u) return;
-            const uint32_t one = 1u << (2 * (b & 15));
-            if (b < 16) cl -= one;
-            else ch -= one;
+        auto dec = [&](uint64_t &C, int b) {
+            if (level(C, b) != 0u) C -= 1ull << (2 * b);
         };
-        uint32_t *rlist = reinterpret_cast<uint32_t *>(hist);  // (group, cl, ch) of groups to refine
+        uint32_t *rlist = reinterpret_cast<uint32_t *>(hist);  // (group, counters lo, hi) of groups to refine
         if (threadIdx.x == 0) mm[0] = 0;
         __syncthreads();
         for (int g = threadIdx.x; g < run; g += TH) {
-            uint32_t cl = 0, ch = 0, mask = 0;
-            bool pad_seen = false;
-            for (int k = 0; k < 32; ++k) {
-                const int p = k * run + g;
-                if (p >= n) {
-                    if (!pad_seen) inc(cl, ch, n & 31);  // the padding word, read as a broadcast
-                    pad_seen = true;
-                    continue;
-                }
-                const int i = (int)(skey[p] & imask);
+            uint64_t C = 0;
+            uint32_t mask = 0;
+            const int kend = min(32, (n - g + run - 1) / run);  // entries k * run + g < n
+            for (int k = 0; k < kend; ++k) {
+                const int i = (int)(skey[k * run + g] & imask);
                 const int ba = i & 31, bb = rot_b(i) & 31;
-                if (i < L.nb && level(cl, ch, bb) < level(cl, ch, ba)) { inc(cl, ch, bb); mask |= 1u << k; }
-                else inc(cl, ch, ba);
+                const uint32_t la = level(C, ba), lb = level(C, bb);
+                const bool tob = i < L.nb && lb < la;
+                const int c = tob ? bb : ba;
+                if ((tob ? lb : la) != 3u) C += 1ull << (2 * c);
+                mask |= (uint32_t)tob << k;
             }
+            if (kend < 32) inc(C, n & 31);  // the padding word, read as a broadcast
             gchoice[g] = mask;
-            if (kPkRefinePasses > 0 && (((cl & (cl >> 1)) | (ch & (ch >> 1))) & 0x55555555u)) {
+            if (kPkRefinePasses > 0 && ((C & (C >> 1)) & 0x5555555555555555ull)) {
                 const int q = atomicAdd(&mm[0], 1);
                 rlist[3 * q] = (uint32_t)g;
-                rlist[3 * q + 1] = cl;
-                rlist[3 * q + 2] = ch;
+                rlist[3 * q + 1] = (uint32_t)C;
+                rlist[3 * q + 2] = (uint32_t)(C >> 32);
             }
         }
         __syncthreads();
         const int nref = mm[0];
         for (int q = threadIdx.x; q < nref; q += TH) {
             const int g = (int)rlist[3 * q];
-            uint32_t cl = rlist[3 * q + 1], ch = rlist[3 * q + 2], mask = gchoice[g];
+            uint64_t C = (uint64_t)rlist[3 * q + 1] | ((uint64_t)rlist[3 * q + 2] << 32);
+            uint32_t mask = gchoice[g];
+            const int kend = min(32, (n - g + run - 1) / run);
             for (int pass = 0; pass < kPkRefinePasses; ++pass)
-                for (int k = 0; k < 32; ++k) {
-                    const int p = k * run + g;
-                    if (p >= n) break;
-                    const int i = (int)(skey[p] & imask);
+                for (int k = 0; k < kend; ++k) {
+                    const int i = (int)(skey[k * run + g] & imask);
                     if (i >= L.nb) continue;
                     const int ba = i & 31, bb = rot_b(i) & 31;
                     const bool onb = (mask >> k) & 1u;
                     const int cur = onb ? bb : ba, oth = onb ? ba : bb;
-                    if (level(cl, ch, cur) > level(cl, ch, oth) + 1) {
-                        dec(cl, ch, cur);
-                        inc(cl, ch, oth);
+                    if (level(C, cur) > level(C, oth) + 1) {
+                        dec(C, cur);
+                        inc(C, oth);
                         mask ^= 1u << k;
                     }
                 }
