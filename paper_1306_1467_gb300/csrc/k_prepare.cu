@@ -645,24 +645,44 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
         }
         __syncthreads();
     }
+    // the run-interleaved write: one 16-byte chunk (8 entries) per thread;
+    // chunk c holds entries t * 8 .. t * 8 + 7 of lane run k (c = t * 32 + k),
+    // consecutive positions p0 .. p0 + 7 of the value order
     bool bad = false;
-    for (int P = threadIdx.x; P < npad; P += TH) {
-        const int p = logical_of(P, run);
-        uint16_t e;
-        if (p < n) {
-            const uint32_t cp = skey[p];
-            const bool step = (p == n - 1) || ((cp >> ib) < (skey[p + 1] >> ib));
-            int word = (int)(cp & imask);
-            if (L.dual) {
-                const int k = (P >> 3) & 31, g = (P >> 8) * kChunkElems + (P & 7);
-                if ((gchoice[g] >> k) & 1u) word = L.off_b + rot_b(word);
-            }
-            bad |= word >= L.words || word == n;
-            e = make_entry(word, step, P);
-        } else {
-            e = make_entry(n, false, P);
+    for (int c = threadIdx.x; c < npad / kChunkElems; c += TH) {
+        const int k = c & 31, t = c >> 5;
+        const int p0 = k * run + t * kChunkElems;
+        uint32_t cp[kChunkElems + 1];
+        const uint4 lo4 = *reinterpret_cast<const uint4 *>(skey + p0);
+        const uint4 hi4 = *reinterpret_cast<const uint4 *>(skey + p0 + 4);
+        cp[0] = lo4.x; cp[1] = lo4.y; cp[2] = lo4.z; cp[3] = lo4.w;
+        cp[4] = hi4.x; cp[5] = hi4.y; cp[6] = hi4.z; cp[7] = hi4.w;
+        cp[8] = p0 + kChunkElems < n ? skey[p0 + kChunkElems] : 0u;
+        uint32_t gc[kChunkElems] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        if (L.dual) {
+            const uint4 g0 = *reinterpret_cast<const uint4 *>(gchoice + t * kChunkElems);
+            const uint4 g1 = *reinterpret_cast<const uint4 *>(gchoice + t * kChunkElems + 4);
+            gc[0] = g0.x; gc[1] = g0.y; gc[2] = g0.z; gc[3] = g0.w;
+            gc[4] = g1.x; gc[5] = g1.y; gc[6] = g1.z; gc[7] = g1.w;
         }
-        out[P] = e;
+        uint32_t wv[kChunkElems / 2];
+#pragma unroll
+        for (int j = 0; j < kChunkElems; ++j) {
+            const int p = p0 + j;
+            uint16_t e;
+            if (p < n) {
+                const bool step = (p == n - 1) || ((cp[j] >> ib) < (cp[j + 1] >> ib));
+                int word = (int)(cp[j] & imask);
+                if ((gc[j] >> k) & 1u) word = L.off_b + rot_b(word);
+                bad |= word >= L.words || word == n;
+                e = make_entry(word, step, j);
+            } else {
+                e = make_entry(n, false, j);
+            }
+            if (j & 1) wv[j >> 1] |= (uint32_t)e << 16;
+            else wv[j >> 1] = e;
+        }
+        reinterpret_cast<uint4 *>(out)[c] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
     }
     row_written(bad, stat);
 }
