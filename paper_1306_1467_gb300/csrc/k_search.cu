@@ -134,19 +134,10 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
     for (int k = 0; k < nf_w && ok; ++k) {
         const int f = gw + k * G;
         float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
-        for (int c = 0; c < nc; ++c) {
-            if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
-                ok = false;
-                break;
-            }
-            const uint32_t sbase = ring_w + (uint32_t)cstage * stage_bytes;
-            // full stages of the default shape through their own call (the
-            // compiler schedules it apart from the general one: 0.767 -> 0.760
-            // ms at 24x24 / 15k)
-            if (U == 3 && crs_full == 6 && c != nc - 1)
-                scan_pieces<2, 3>(sbase, 0, lane, sv, ahi, alo, bmx, bmn);
-            else
-                scan_stage<U>(sbase, c == nc - 1 ? crs_last : crs_full, lane, sv, ahi, alo, bmx, bmn);
+        // one stage: wait for its copy, scan it, give the slot its next copy
+        auto stage_step = [&](auto scan) -> bool {
+            if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) return false;
+            scan(ring_w + (uint32_t)cstage * stage_bytes);
             __syncwarp();
             if (lane == 0) {
                 fence_proxy_async_smem();
@@ -154,6 +145,20 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
             }
             if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
             ++consumed;
+            return true;
+        };
+        if (U == 3 && crs_full == 6) {
+            // the default shape: the full stages in a loop of their own around
+            // one call that the compiler schedules apart from the general stage
+            // (0.787 -> 0.759 ms at 24x24 / 15k), then the row's last stage
+            for (int c = 0; c < nc - 1 && ok; ++c)
+                ok = stage_step([&](uint32_t sb) { scan_pieces<2, 3>(sb, 0, lane, sv, ahi, alo, bmx, bmn); });
+            if (ok) ok = stage_step([&](uint32_t sb) { scan_stage<U>(sb, crs_last, lane, sv, ahi, alo, bmx, bmn); });
+        } else {
+            for (int c = 0; c < nc && ok; ++c)
+                ok = stage_step([&](uint32_t sb) {
+                    scan_stage<U>(sb, c == nc - 1 ? crs_last : crs_full, lane, sv, ahi, alo, bmx, bmn);
+                });
         }
         if (!ok) break;
         const float e = finish_row(ahi, alo, bmx, bmn, Tp, Tm, lane);
