@@ -160,17 +160,10 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
         for (int k = 0; k < nrows && ok; ++k) {
             const int64_t f = W.f0 + warp + (int64_t)k * nw;
             float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
-            for (int c = 0; c < nc; ++c) {
-                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t sbase = ring_w + (uint32_t)cstage * stage_bytes;
-                if (U == 3 && stage_lines == 24 && c != nc - 1)  // full stages of the default shape
-                    scan_pieces<2, 3>(sbase, 0, lane, sv, ahi, alo, bmx, bmn);
-                else
-                    scan_stage<U>(sbase, min(stage_lines, lines - c * stage_lines) >> 2, lane, sv, ahi, alo,
-                                  bmx, bmn);
+            // one stage: wait for its copy, scan it, give the slot its next copy
+            auto stage_step = [&](auto scan) -> bool {
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) return false;
+                scan(ring_w + (uint32_t)cstage * stage_bytes);
                 __syncwarp();
                 if (lane == 0) {
                     fence_proxy_async_smem();
@@ -178,6 +171,19 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
                 }
                 if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
                 ++consumed;
+                return true;
+            };
+            const int last_crs = (lines - (nc - 1) * stage_lines) >> 2;
+            if (U == 3 && stage_lines == 24) {
+                // the default shape: full stages in a loop of their own, then the row's last
+                for (int c = 0; c < nc - 1 && ok; ++c)
+                    ok = stage_step([&](uint32_t sb) { scan_pieces<2, 3>(sb, 0, lane, sv, ahi, alo, bmx, bmn); });
+                if (ok) ok = stage_step([&](uint32_t sb) { scan_stage<U>(sb, last_crs, lane, sv, ahi, alo, bmx, bmn); });
+            } else {
+                for (int c = 0; c < nc && ok; ++c)
+                    ok = stage_step([&](uint32_t sb) {
+                        scan_stage<U>(sb, c == nc - 1 ? last_crs : stage_lines >> 2, lane, sv, ahi, alo, bmx, bmn);
+                    });
             }
             if (!ok) break;
             const float e = finish_row(ahi, alo, bmx, bmn, Tp, Tm, lane);
@@ -325,17 +331,10 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
         for (int k = 0; k < nrows && ok; ++k) {
             const int f = f0 + k * nw;
             float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
-            for (int c = 0; c < nc; ++c) {
-                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t sbase = ring_w + (uint32_t)cstage * stage_bytes;
-                if (U == 3 && stage_lines == 24 && c != nc - 1)  // full stages of the default shape
-                    scan_pieces<2, 3>(sbase, 0, lane, sv, ahi, alo, bmx, bmn);
-                else
-                    scan_stage<U>(sbase, min(stage_lines, lines - c * stage_lines) >> 2, lane, sv, ahi, alo,
-                                  bmx, bmn);
+            // one stage: wait for its copy, scan it, give the slot its next copy
+            auto stage_step = [&](auto scan) -> bool {
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) return false;
+                scan(ring_w + (uint32_t)cstage * stage_bytes);
                 __syncwarp();
                 if (lane == 0) {
                     fence_proxy_async_smem();
@@ -343,6 +342,19 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
                 }
                 if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
                 ++consumed;
+                return true;
+            };
+            const int last_crs = (lines - (nc - 1) * stage_lines) >> 2;
+            if (U == 3 && stage_lines == 24) {
+                // the default shape: full stages in a loop of their own, then the row's last
+                for (int c = 0; c < nc - 1 && ok; ++c)
+                    ok = stage_step([&](uint32_t sb) { scan_pieces<2, 3>(sb, 0, lane, sv, ahi, alo, bmx, bmn); });
+                if (ok) ok = stage_step([&](uint32_t sb) { scan_stage<U>(sb, last_crs, lane, sv, ahi, alo, bmx, bmn); });
+            } else {
+                for (int c = 0; c < nc && ok; ++c)
+                    ok = stage_step([&](uint32_t sb) {
+                        scan_stage<U>(sb, c == nc - 1 ? last_crs : stage_lines >> 2, lane, sv, ahi, alo, bmx, bmn);
+                    });
             }
             if (!ok) break;
             const float e = finish_row(ahi, alo, bmx, bmn, Tp, Tm, lane);
@@ -469,17 +481,10 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
         for (int k = 0; k < nrows && ok; ++k) {
             const int f = gw + k * G;
             float ahi = 0.f, alo = 0.f, bmx = -INFINITY, bmn = INFINITY;
-            for (int c = 0; c < nc; ++c) {
-                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) {
-                    ok = false;
-                    break;
-                }
-                const uint32_t sbase = ring_w + (uint32_t)cstage * stage_bytes;
-                if (U == 3 && stage_lines == 24 && c != nc - 1)  // full stages of the default shape
-                    scan_pieces<2, 3>(sbase, 0, lane, sv, ahi, alo, bmx, bmn);
-                else
-                    scan_stage<U>(sbase, min(stage_lines, lines - c * stage_lines) >> 2, lane, sv, ahi, alo,
-                                  bmx, bmn);
+            // one stage: wait for its copy, scan it, give the slot its next copy
+            auto stage_step = [&](auto scan) -> bool {
+                if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar_w + 8u * (uint32_t)cstage, cpar))) return false;
+                scan(ring_w + (uint32_t)cstage * stage_bytes);
                 __syncwarp();
                 if (lane == 0) {
                     fence_proxy_async_smem();
@@ -487,6 +492,19 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
                 }
                 if (++cstage == stages) { cstage = 0; cpar ^= 1u; }
                 ++consumed;
+                return true;
+            };
+            const int last_crs = (lines - (nc - 1) * stage_lines) >> 2;
+            if (U == 3 && stage_lines == 24) {
+                // the default shape: full stages in a loop of their own, then the row's last
+                for (int c = 0; c < nc - 1 && ok; ++c)
+                    ok = stage_step([&](uint32_t sb) { scan_pieces<2, 3>(sb, 0, lane, sv, ahi, alo, bmx, bmn); });
+                if (ok) ok = stage_step([&](uint32_t sb) { scan_stage<U>(sb, last_crs, lane, sv, ahi, alo, bmx, bmn); });
+            } else {
+                for (int c = 0; c < nc && ok; ++c)
+                    ok = stage_step([&](uint32_t sb) {
+                        scan_stage<U>(sb, c == nc - 1 ? last_crs : stage_lines >> 2, lane, sv, ahi, alo, bmx, bmn);
+                    });
             }
             if (!ok) break;
             const float e = finish_row(ahi, alo, bmx, bmn, Tp, Tm, lane);
