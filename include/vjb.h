@@ -119,7 +119,8 @@ typedef struct {
 
 /* Per-launch timing of the rounds run since timing was (re)enabled, from CUDA
  * events recorded on the context's stream around the search kernel and around
- * the whole round (also inside the CUDA graph that vjb_train_strong replays). */
+ * the whole round (with timing on, vjb_train_strong replays each round as two
+ * graphs, the search and the rest, with the events between them). */
 typedef struct {
     int32_t rounds;           /* rounds timed                                   */
     int32_t pad;
@@ -171,8 +172,11 @@ int vjb_build_integral(vjb_ctx *ctx);
  * the per-feature sample order used by every round: samples sorted by value,
  * ties by sample index.  *count receives F.  If `out` is not NULL it must
  * hold F entries (host) and receives the feature list.  A second call returns
- * the same list without recomputing.  Errors: VJB_ESTATE before
- * vjb_build_integral; VJB_EINVAL (count NULL); VJB_ENOMEM; VJB_ECUDA. */
+ * the same list without recomputing.  The sort checks every table entry it
+ * writes (a word inside the weight array) and counts the rows written; a
+ * table that fails the check is not used.  Errors: VJB_ESTATE before
+ * vjb_build_integral; VJB_EINVAL (count NULL); VJB_ENOMEM; VJB_EDEVICE (the
+ * table check failed); VJB_ECUDA. */
 int vjb_enumerate_haar(vjb_ctx *ctx, int64_t *count, vjb_feature *out);
 
 /* ---- step 3: one boosting round (Sec. 2.3 steps 1-4) --------------------
@@ -374,8 +378,10 @@ int vjb_batch_get_timing(vjb_batch *b, vjb_timing *out);
  * until its sorted table fits the free part of the table budget and a job
  * slot is free; later requests may overtake one that does not fit, at most 8
  * times.  An admitted request is prepared (integral images, features, sorted
- * table) by a worker thread on its own stream while the batch keeps training
- * the others, joins the batch at the next round and leaves it when it has
+ * table) by a worker thread on a low-priority stream while the batch keeps
+ * training the others on a high-priority one (the worker also frees the
+ * contexts of finished requests), joins the batch at the next round and
+ * leaves it when it has
  * kept `rounds` stumps (or stops early); its table space then goes to the
  * requests still waiting.  Each request's stumps and weights are those of a
  * plain run of the same job (see the batch section).
