@@ -389,18 +389,21 @@ static cudaError_t launch_sort_ipt(const int32_t *ii_t, int ii_stride, int w, co
     return cudaGetLastError();
 }
 
-// ---- K3, packed variant ----------------------------------------------------------------
+// ---- K3, packed variant (the one every row goes through first) ---------------------------
 // The same stable sort for rows whose items fit one 32-bit word: value - min
-// in the high bits above a sample index of ib bits.  That holds when
-// n <= 16384 (ib <= 14) and a value span below 2^18 (every window of at most
-// 1028 pixels, 255 * w * h < 2^18).  Items move as one word, the radix digit
-// has 9 bits (two passes cover an 18-bit span), and a CTA of 512 threads
-// needs about 100 KiB of shared memory, so two rows sort per SM at a time.
-// Only the value bits are sorted; the starting index order and stable passes
-// order ties by sample index.  A pass ranks each item once: while the warps
-// count their digits, every item records its rank among its warp's earlier
-// items of the same digit (two 16-bit ranks per register), so the scatter
-// after the CTA-wide scan needs only the scanned offsets.
+// in the high bits above a sample index of ib bits (ib = 14 up to 16,384
+// samples with 512-thread CTAs, two per SM; 15 above, with 1024-thread CTAs).
+// A row whose value span does not fit next to its index is listed for the
+// two-word sort above.  Only the value bits are sorted, in one pass when the
+// span has at most 9 bits and in two passes over digits of half the span's
+// bits (5 to 9) otherwise; the starting index order and stable passes order
+// ties by sample index.  A pass ranks each item once: while the warps count
+// their digits (the lanes holding the same digit come from one ballot per
+// digit bit), every item records its rank among its warp's earlier items of
+// the same digit (in shared memory, or two 16-bit ranks per register), so the
+// scatter after the CTA-wide scan needs only the scanned offsets.  Then the
+// bank choice of the two weight copies and the run-interleaved write, one
+// 16-byte chunk per thread.
 constexpr int kPkThreads = 512;
 constexpr int kPkRefinePasses = 1;  // a second pass buys no search time
 constexpr int kPkDigitBits = 9;
