@@ -101,7 +101,17 @@ __device__ __forceinline__ void scan_stage(uint32_t sbase, int crs, int lane, co
     } else {
         for (; t + 2 * U <= crs; t += 2 * U) scan_pieces<U, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
     }
-    for (; t + 2 <= crs; t += 2) scan_pieces<1, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+    // what is left of a row's last stage: two 16-entry pieces at a time, then
+    // one piece of 24, 16 or 8 (0.7589 -> 0.7554 ms at 24x24 / 15k, +1% at
+    // 4,000 samples, against single pieces of 16)
+    for (; t + 4 <= crs; t += 4) scan_pieces<2, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+    if (t + 3 <= crs) {
+        scan_pieces<1, 3>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+        t += 3;
+    } else if (t + 2 <= crs) {
+        scan_pieces<1, 2>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
+        t += 2;
+    }
     if (t < crs) scan_pieces<1, 1>(sbase, t, lane, sv, ahi, alo, bmx, bmn);
 }
 
