@@ -166,6 +166,27 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (x86 `model name`, else the Arm implementer
+    and part numbers), for the CPU baseline's record."""
+    import platform
+    info = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    info.setdefault(k.strip(), v.strip())
+    except OSError:
+        pass
+    if info.get("model name"):
+        return info["model name"]
+    if "CPU implementer" in info:
+        return (f"{platform.machine()} implementer {info['CPU implementer']} "
+                f"part {info.get('CPU part', '?')}")
+    return platform.machine() or "unknown"
+
+
 def cpu_baseline(px, y, rounds: int, every: int = 1, sample_rounds: int = 2):
     """The CPU oracle as it stands, on a bounded sample of the workload: every
     `every`-th feature, its values, value orders and `sample_rounds` rounds;
@@ -190,7 +211,8 @@ def cpu_baseline(px, y, rounds: int, every: int = 1, sample_rounds: int = 2):
     round_s = (t2 - t1) / sample_rounds * scale
     job_s = prep_s + rounds * round_s
     del np
-    return {"value": rounds / job_s, "unit": "rounds/s", "cores": O.num_threads(), "kind": "oracle",
+    return {"value": rounds / job_s, "unit": "rounds/s", "cores": O.num_threads(), "cpu": cpu_model(),
+            "kind": "oracle",
             "sample": (f"{sub.shape[0]} of {desc.shape[0]} features (every {every}), all {n} windows: "
                        f"values + stable sort + {sample_rounds} FP64 rounds, scaled to all features "
                        f"and {rounds} rounds"),

@@ -46,3 +46,9 @@ def test_traffic_is_null_once_the_kernel_changed(tmp_path, monkeypatch):
 def test_traffic_is_null_without_a_summary(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "PROFILE", str(tmp_path / "missing.txt"))
     assert bench._traffic() is None
+
+
+def test_cpu_model_is_named():
+    # the CPU baseline names the host CPU beside its thread count
+    m = bench.cpu_model()
+    assert isinstance(m, str) and m and m != "unknown"
