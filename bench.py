@@ -46,6 +46,8 @@ def _args():
     p.add_argument("--workload", default="paper_24x24_15k")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-batch", action="store_true",
+                   help="leave the batched-vs-plain comparison out of the default line")
     p.add_argument("--precision", action="store_true",
                    help="precision form: 300 rounds from log-uniform weights, search vs FP64")
     p.add_argument("--oracle-rounds", type=int, default=6,
@@ -187,14 +189,17 @@ def cpu_model() -> str:
     return platform.machine() or "unknown"
 
 
-def cpu_baseline(px, y, rounds: int, every: int = 1, sample_rounds: int = 2):
+def cpu_baseline(px, y, rounds: int, every: int = 1, sample_rounds: int = 2, threads: int = 0):
     """The CPU oracle as it stands, on a bounded sample of the workload: every
     `every`-th feature, its values, value orders and `sample_rounds` rounds;
-    the job time is scaled to all features and `rounds` rounds."""
+    the job time is scaled to all features and `rounds` rounds.  `threads` > 0
+    runs the oracle's loops on that many host threads (0: all of them)."""
     import numpy as np
 
     import oracle as O
     n, H, W = px.shape
+    all_threads = O.num_threads()
+    O.set_num_threads(threads if threads > 0 else all_threads)
     desc, _ = O.haar_enumerate(W, H)
     sub = desc[::every]
     t0 = time.perf_counter()
@@ -210,8 +215,10 @@ def cpu_baseline(px, y, rounds: int, every: int = 1, sample_rounds: int = 2):
     prep_s = (t1 - t0) * scale
     round_s = (t2 - t1) / sample_rounds * scale
     job_s = prep_s + rounds * round_s
+    cores = O.num_threads()
+    O.set_num_threads(all_threads)
     del np
-    return {"value": rounds / job_s, "unit": "rounds/s", "cores": O.num_threads(), "cpu": cpu_model(),
+    return {"value": rounds / job_s, "unit": "rounds/s", "cores": cores, "cpu": cpu_model(),
             "kind": "oracle",
             "sample": (f"{sub.shape[0]} of {desc.shape[0]} features (every {every}), all {n} windows: "
                        f"values + stable sort + {sample_rounds} FP64 rounds, scaled to all features "
@@ -299,7 +306,7 @@ def run_ours(a, ws, rank, local):
     for _ in range(max(a.warmup, 1)):
         nf, _ = job(False)
     info0 = tr.info()
-    tr.set_timing(True)
+    tr.set_timing(False)  # value: no per-round timing events in the timed region
     uuid = None
     try:
         uuid = str(torch.cuda.get_device_properties(dev).uuid)
@@ -324,9 +331,15 @@ def run_ours(a, ws, rank, local):
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    tm = tr.timing()
     info1 = tr.info()
     launches = info1["launches"] - info0["launches"]
+
+    # roofline: a second pass of the same jobs with CUDA events around every
+    # search launch (a round then replays as two graphs with the events between)
+    tr.set_timing(True)
+    for _ in range(a.steps):
+        job(False)
+    tm = tr.timing()
     tr.set_timing(False)
 
     # setup vs rounds split of one job (extra run, untimed for `value`)
@@ -390,11 +403,15 @@ def run_ours(a, ws, rank, local):
                      "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
                      "traffic": traffic, "algorithmic_bytes_per_launch": search_bytes,
                      "avg_launch_ms": avg_search_ms, "min_launch_ms": tm["search_ms_min"],
-                     "max_launch_ms": tm["search_ms_max"], "launches_timed": tm["rounds"]},
+                     "max_launch_ms": tm["search_ms_max"], "launches_timed": tm["rounds"],
+                     "timed": "a second pass of the same jobs with per-launch events"},
         "gpu_launches": int(launches),
         "rounds_only_per_s": 1000.0 * rounds / rounds_ms,
         "setup_ms": setup_ms,
-        "round_ms": tm["round_ms_total"] / max(tm["rounds"], 1),
+        # a round's share of the timed step (no per-round events), and as the
+        # second pass's events saw it
+        "round_ms": (ms / a.steps - setup_ms) / rounds,
+        "round_ms_with_events": tm["round_ms_total"] / max(tm["rounds"], 1),
     }
     if e2e:
         line["e2e"] = e2e
@@ -402,7 +419,15 @@ def run_ours(a, ws, rank, local):
         line["clocks"] = ck
     if ws == 1 and rank == 0 and not a.no_cpu:
         line["cpu_baseline"] = cpu_baseline(px, y, rounds)
+        one = cpu_baseline(px, y, rounds, every=16, sample_rounds=2, threads=1)
+        line["cpu_baseline"]["single_thread"] = {k: one[k] for k in ("value", "unit", "cores", "sample", "job_s",
+                                                                      "prep_s", "round_s", "measured_s")}
     tr.close()
+    del d_px, d_y
+    if ws == 1 and rank == 0 and not a.no_batch:
+        torch.cuda.synchronize(dev)
+        torch.cuda.empty_cache()
+        line["batched"] = batch_comparison(a, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -479,31 +504,54 @@ def run_precision_report(a):
     print(json.dumps(line), flush=True)
 
 
+def _make_job(shape):
+    """Windows and labels of one batching job (runs in a worker process)."""
+    from paper_1306_1467_gb300 import synth
+    p, q, h, w, sd = shape
+    return synth.make_windows(p, q, h, w, seed=sd)
+
+
 def batch_comparison(a, device: int = 0) -> dict:
     """Batching form: `--batch-jobs` independent 24x24 jobs (N uniform in
     2,000..20,000, positive fraction 0.2..0.5), `--batch-rounds` rounds each,
     trained (1) one after another through the plain path and (2) together in
-    one batch (one launch of each round kernel per round, CUDA graph, launch
-    shape from the batch autotuner).  Reports both throughputs on this GPU and
-    whether every job's stumps are identical in the two."""
+    one batch (one launch of each round kernel per round for all jobs, CUDA
+    graph, launch shape from the batch autotuner).  Both arms are timed on
+    the device over their rounds only (the one-time sort of each job is the
+    same work in both), with no per-round timing events; the batched search's
+    roofline comes from a few extra-timed rounds.  Reports both throughputs,
+    the speedup and whether every job's stumps are identical in the two."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
     import torch
 
     from paper_1306_1467_gb300 import synth, vjb
 
     shapes = synth.batch_jobs(a.batch_jobs, seed=1309, n_lo=a.batch_n[0], n_hi=a.batch_n[1])
-    data = [synth.make_windows(p, q, h, w, seed=sd) for (p, q, h, w, sd) in shapes]
+    t_gen = time.perf_counter()
+    # the host generator costs about 0.4 s per job: draw the jobs in worker
+    # processes started with spawn (this process already holds a CUDA context)
+    with cf.ProcessPoolExecutor(max_workers=min(16, os.cpu_count() or 1),
+                                mp_context=mp.get_context("spawn")) as ex:
+        data = list(ex.map(_make_job, shapes))
+    gen_s = time.perf_counter() - t_gen
     R = a.batch_rounds
     nf = None
     byts = []
-    # (1) plain: one context, the jobs one after another; rounds timed on the device
     stream = torch.cuda.Stream(device=device)
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    # (1) plain: one context, the jobs one after another; each job's rounds
+    # timed on the device
     plain_ms, plain_stumps = 0.0, []
     with vjb.Trainer(device, stream=stream.cuda_stream) as tr:
         for px, y in data:
             nf = tr.prepare(px, y).shape[0]
             byts.append(2.0 * nf * px.shape[0])
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
+            e0, e1 = ev(), ev()
             e0.record(stream)
             st, stumps = tr.train_strong(R)
             e1.record(stream)
@@ -514,45 +562,54 @@ def batch_comparison(a, device: int = 0) -> dict:
     # (2) batched
     budget = sum(vjb.Batch.table_bytes(px.shape[0], px.shape[1], px.shape[2]) for px, _ in data)
     t0 = time.perf_counter()
-    b = vjb.Batch(budget, device=device)
+    b = vjb.Batch(budget, device=device, stream=stream.cuda_stream)
     ids = [b.add_job(px, y, R) for px, y in data]
     setup_s = time.perf_counter() - t0
     tuned = b.autotune(trial_rounds=2)
     b_trials = b.trials
     info = b.info()
+    # a few rounds with events around every batched search (the roofline)
     b.set_timing(True)
-    t1 = time.perf_counter()
-    rest = b.train()
-    batch_s = time.perf_counter() - t1
+    roof_rounds = b.train(min(4, max(R - tuned - 1, 0)))
     tm = b.timing()
+    b.set_timing(False)
+    # the rest, no per-round events: job-rounds per second of device time
+    done0 = sum(b.job_state(j)[0] for j in ids)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    rest = b.train()
+    e1.record(stream)
+    e1.synchronize()
+    batch_ms = e0.elapsed_time(e1)
+    job_rounds = sum(b.job_state(j)[0] for j in ids) - done0
     equal = sum(b.stumps(j) == ps for j, ps in zip(ids, plain_stumps))
     b.close()
     peak, peak_src = _peak()
     round_bytes = sum(byts)
     plain_rps = len(data) * R / (plain_ms / 1000.0)
-    batch_rps = len(data) * rest / batch_s if rest else 0.0
-    gbs = round_bytes * rest / batch_s / 1e9
+    batch_rps = job_rounds / (batch_ms / 1000.0) if rest else 0.0
     search_ms = tm["search_ms_total"] / max(tm["rounds"], 1)
     search_gbs = round_bytes / (search_ms / 1000.0) / 1e9 if tm["rounds"] else 0.0
     return {"workload": f"{len(data)} jobs, 24x24, N uniform {a.batch_n[0]}-{a.batch_n[1]} "
                         f"(sum {sum(p + q for p, q, *_ in shapes)}), "
                         f"positive fraction 0.2-0.5, {R} rounds each, seed 1309",
-            "features_per_job": nf, "table_bytes": budget,
+            "features_per_job": nf, "table_bytes": budget, "host_generation_s": gen_s,
+            "timed": "rounds only, CUDA events on the device, no per-round events",
             "plain": {"job_rounds_per_s": plain_rps, "ms_rounds_total": plain_ms,
                       "gbs": round_bytes * R / (plain_ms / 1000.0) / 1e9},
-            "batched": {"job_rounds_per_s": batch_rps, "batch_round_ms": 1000.0 * batch_s / max(rest, 1),
-                        "gbs": gbs, "frac": gbs / peak, "peak": peak, "peak_source": f"{peak_src} hbm_gbs",
-                        "rounds_timed": rest, "autotune_rounds": tuned,
-                        "shape": {**{k: info[k] for k in ("warps", "stages", "unroll")},
+            "batched": {"job_rounds_per_s": batch_rps, "batch_round_ms": batch_ms / max(rest, 1),
+                        "gbs": round_bytes * rest / (batch_ms / 1000.0) / 1e9, "rounds_timed": rest,
+                        "job_rounds_timed": job_rounds, "autotune_rounds": tuned, "roofline_rounds": roof_rounds,
+                        "shape": {**{k: info[k] for k in ("warps", "stages", "unroll", "box_lines")},
                                   "schedule": {-1: "partitioned", -2: "interleaved"}.get(
                                       info["rows_per_warp"], f"work queue, {info['rows_per_warp']} rows per warp and item")},
-                        "setup_s": setup_s, "launches_per_round": 6,
-                        "roofline": {"kernel": "k_bscreen", "bound": "hbm", "achieved": search_gbs, "peak": peak,
-                                     "unit": "GB/s", "frac": search_gbs / peak,
-                                     "algorithmic_bytes_per_launch": round_bytes, "avg_launch_ms": search_ms,
-                                     "min_launch_ms": tm["search_ms_min"], "max_launch_ms": tm["search_ms_max"],
-                                     "launches_timed": tm["rounds"],
-                                     "round_ms": tm["round_ms_total"] / max(tm["rounds"], 1)}},
+                        "setup_s": setup_s, "launches_per_round": 6},
+            "roofline": {"kernel": "k_bscreen", "bound": "hbm", "achieved": search_gbs, "peak": peak,
+                         "peak_source": f"{peak_src} hbm_gbs", "unit": "GB/s", "frac": search_gbs / peak,
+                         "algorithmic_bytes_per_launch": round_bytes, "avg_launch_ms": search_ms,
+                         "min_launch_ms": tm["search_ms_min"], "max_launch_ms": tm["search_ms_max"],
+                         "launches_timed": tm["rounds"],
+                         "round_ms_with_events": tm["round_ms_total"] / max(tm["rounds"], 1)},
             "autotune_trials": b_trials,
             "speedup": batch_rps / plain_rps,
             "identical_jobs": f"{equal}/{len(data)}"}

@@ -453,9 +453,9 @@ int vjb_server_round_times(vjb_server *s, int64_t first, int32_t count, float *m
 
 /* ---- allocation-free search ----------------------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
- * that cannot allocate device memory when they want a search -- a host that
- * is capturing its own CUDA graph, a real-time loop whose memory is fixed up
- * front, or a framework whose pool owns all device memory.
+ * that cannot allocate device memory when they want a search -- a real-time
+ * loop whose memory is fixed up front (a cudaMalloc can wait on the whole
+ * device), or a framework whose pool owns all device memory.
  *
  * vjb_screen_noalloc runs the per-round FP32 screen (the search kernel of
  * vjb_train_round, without its compensated re-scan) over a caller-owned
@@ -478,9 +478,12 @@ int vjb_server_round_times(vjb_server *s, int64_t first, int32_t count, float *m
  *   t_pos, t_neg  face and non-face weight totals (finite, >= 0).
  *   ctas          CTAs to launch, 0 = one per SM; at most 1024.
  *   feature_err   [nfeat] float out: each feature's least stump error.
- *   best_err      [1] float out: the smallest of them.
+ *   best_err      [1] float out: the smallest of them; NaN if a TMA wait
+ *                 timed out.
  *   best_feature  [1] int32 out: its feature (lowest index on ties), or -1
- *                 if a TMA wait timed out.
+ *                 if a TMA wait timed out (feature_err is then undefined)
+ *                 or no feature has an error that is not NaN (NaN weights;
+ *                 best_err is then +inf).
  *   cuda_stream   cudaStream_t to run on (NULL: the legacy default stream).
  * The call is asynchronous on the stream.  The first call on a device does
  * that device's set-up (the scratch array's device address, the kernel's

@@ -61,6 +61,7 @@ def _load():
         P = C.c_void_p
         i64, i32 = C.c_int64, C.c_int32
         lib.orc_num_threads.restype = C.c_int
+        lib.orc_set_num_threads.argtypes = [C.c_int]
         lib.orc_haar_enumerate.argtypes = [C.c_int, C.c_int, P, P]
         lib.orc_haar_enumerate.restype = i64
         lib.orc_integral.argtypes = [P, i64, C.c_int, C.c_int, P]
@@ -90,6 +91,11 @@ def _p(a: np.ndarray):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(k: int) -> None:
+    """Threads the oracle's parallel loops use from now on (k > 0)."""
+    _load().orc_set_num_threads(int(k))
 
 
 def haar_enumerate(W: int, H: int):

@@ -92,6 +92,16 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the later parallel loops (the benchmark times 1 and all). */
+void orc_set_num_threads(int k)
+{
+#ifdef _OPENMP
+    if (k > 0) omp_set_num_threads(k);
+#else
+    (void)k;
+#endif
+}
+
 /* ---------------------------------------------------------------- Sec. 2.2 */
 
 /* Enumerate every feature of a W x H window in canonical order.  desc may be

@@ -302,10 +302,9 @@ cudaError_t launch_rescan(const JobDesc &J, int grid, cudaStream_t st) {
 namespace vjb {
 
 // ---- allocation-free variant of the search kernel --------------------------------------
-// Some callers cannot call cudaMalloc at the moment they want a search: a host
-// that is stream-capturing its own CUDA graph, a real-time loop whose memory
-// is fixed up front, or a framework that hands all device memory to its own
-// pool.  vjb_screen_noalloc serves them: the caller passes the sorted table,
+// Some callers cannot call cudaMalloc at the moment they want a search: a
+// real-time loop whose memory is fixed up front, or a framework that hands all
+// device memory to its own pool.  vjb_screen_noalloc serves them: the caller passes the sorted table,
 // the signed weights and the outputs, and the only scratch the search needs --
 // one (error, feature) partial per CTA plus a completion counter for the
 // last-CTA reduction -- lives in the file-scope array below.  Every GPU that
@@ -489,8 +488,9 @@ __global__ void __launch_bounds__(512, 1)
             const int32_t f = (int32_t)((volatile uint32_t *)scratch)[kNoAllocMaxCtas + b];
             if (e < m || (e == m && f < mf)) { m = e; mf = f; }
         }
+        // a wait that gave up leaves rows unscanned: no minimum to report
         const bool failed = ((volatile uint32_t *)scratch)[kNoAllocFlags] != 0u;
-        *best_err = m;
+        *best_err = failed ? __int_as_float(0x7fc00000) : m;
         *best_feature = failed ? -1 : mf;
         scratch[kNoAllocDone] = 0u;  // the next call starts from zero
     }
