@@ -121,6 +121,21 @@ __device__ __forceinline__ void scan_stage(uint32_t sbase, int crs, int lane, co
 // plain FP32 over the run totals rounded once (it adds at most 6u of the
 // weight total to the screening bound of k_search.cu; a double-float scan
 // here cost about 2% of the search at 15,000 samples and 13% at 2,500).
+//
+// The row's error is min over lanes of min(Tp - x_l, Tm + y_l), x_l and y_l the
+// lane's best prefixes placed on its offset, and of Tp and Tm (split 0): the
+// same floats as Tp - max x_l and Tm + min y_l, since a min does not round.
+// So each lane forms its own candidate and one integer min reduction
+// (redux.sync on an order-preserving key of the float) ends the row: a
+// shorter chain at every row end than a max and a min of five shuffles each.
+__device__ __forceinline__ int32_t float_order_key(float f) {
+    const int32_t b = __float_as_int(f);
+    return b ^ ((b >> 31) & 0x7fffffff);  // negative floats: reverse their magnitude order
+}
+__device__ __forceinline__ float float_from_order_key(int32_t k) {
+    return __int_as_float(k ^ ((k >> 31) & 0x7fffffff));
+}
+
 __device__ __forceinline__ float finish_row(float ahi, float alo, float bmx, float bmn, float Tp,
                                             float Tm, int lane) {
     float x = ahi + alo;
@@ -131,11 +146,8 @@ __device__ __forceinline__ float finish_row(float ahi, float alo, float bmx, flo
     }
     float excl = __shfl_up_sync(0xffffffffu, x, 1);
     if (lane == 0) excl = 0.f;
-    float MX = warp_max(excl + bmx);
-    float MN = warp_min(excl + bmn);
-    MX = fmaxf(MX, 0.f);
-    MN = fminf(MN, 0.f);
-    return fminf(Tp - MX, Tm + MN);
+    const float e = fminf(fminf(Tp - (excl + bmx), Tm + (excl + bmn)), fminf(Tp, Tm));
+    return float_from_order_key(__reduce_min_sync(0xffffffffu, float_order_key(e)));
 }
 
 // The screened error within which a feature must lie of the smallest one
