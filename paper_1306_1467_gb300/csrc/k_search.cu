@@ -272,28 +272,86 @@ cudaError_t launch_shortlist(const JobDesc &J, const float *bmin, int nbmin, int
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kRescanWarps * 32) k_rescan(const JobDesc J) {
-    if (J.rs->status != VJB_OK || J.rs->forced) return;
+// The compensated re-scan of the shortlist, spread over the SMs: work item i
+// is lane run i % 32 of shortlisted feature i / 32, taken by warp (i / G) % W
+// of CTA i % G (G CTAs of W warps), so that a feature's 32 runs land on 32
+// SMs (one SM doing all 32 was issue-bound: 11.6 us at 24x24 / 15k).  The
+// warp that finishes a feature's last run combines its 32 run results; the
+// warp that completes the last feature picks the round's stump.  Features
+// beyond kRescanSplitCap (only a plateau of ties lists that many) are
+// re-scanned whole, one CTA each.
+constexpr int kRescanCtas = 32;
+constexpr int kRescanCtaWarps = 16;
+static_assert(sizeof(RunResult) == kRunResultBytes, "run result layout");
+
+__device__ __forceinline__ RunResult load_run_result(const RunResult *p) {
+    const volatile uint32_t *w = reinterpret_cast<const volatile uint32_t *>(p);
+    RunResult r;
+    r.total.hi = __uint_as_float(w[0]); r.total.lo = __uint_as_float(w[1]);
+    r.mx.hi = __uint_as_float(w[2]);    r.mx.lo = __uint_as_float(w[3]);
+    r.mn.hi = __uint_as_float(w[4]);    r.mn.lo = __uint_as_float(w[5]);
+    r.smx = (int)w[6];                  r.smn = (int)w[7];
+    return r;
+}
+
+__global__ void __launch_bounds__(kRescanCtaWarps * 32) k_rescan(const JobDesc J) {
+    RoundState *rs = J.rs;
+    if (rs->status != VJB_OK || rs->forced) return;
     __shared__ RunResult rres[32];
-    __shared__ bool last_cta;
-    const int cnt = J.rs->cand_count;
-    for (int c = blockIdx.x; c < cnt; c += gridDim.x) {
-        const Candidate cd = rescan_feature(J, J.cand_ids[c], rres);
-        if (threadIdx.x == 0) J.cands[c] = cd;
+    __shared__ int last_cta;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cnt = rs->cand_count;
+    if (cnt == 0) {  // nothing was listed: stop the job with an error flag
+        if (blockIdx.x == 0 && warp == 0) select_stump_warp(J, 0, lane);
+        return;
     }
-    // the last CTA to finish picks the round's stump
-    if (threadIdx.x == 0) {
+    const int run = J.npad / 32;
+    const int items = min(cnt, kRescanSplitCap) * 32;
+    for (int i = (int)blockIdx.x + (int)gridDim.x * warp; i < items; i += (int)gridDim.x * kRescanCtaWarps) {
+        const int c = i >> 5;
+        const int32_t f = J.cand_ids[c];
+        const RunResult r = rescan_run(J.rows + (size_t)f * J.npad, run, i & 31, J.v, lane);
+        uint32_t prev = 0;
+        if (lane == 0) {
+            J.runres[i] = r;
+            __threadfence();
+            prev = atomicAdd(&J.cand_runs[c], 1u);
+        }
+        if (__shfl_sync(0xffffffffu, prev, 0) != 31u) continue;
+        // this feature's last run: combine its 32 runs
         __threadfence();
-        last_cta = atomicAdd(&J.rs->done_rescan, 1u) == gridDim.x - 1;
+        const Candidate cd = combine_runs(J, f, load_run_result(J.runres + c * 32 + lane), lane);
+        uint32_t done = 0;
+        if (lane == 0) {
+            J.cand_runs[c] = 0u;
+            J.cands[c] = cd;
+            __threadfence();
+            done = atomicAdd(&rs->done_rescan, 1u);
+        }
+        if (__shfl_sync(0xffffffffu, done, 0) == (uint32_t)cnt - 1) {
+            __threadfence();
+            select_stump_warp(J, cnt, lane);
+        }
     }
-    __syncthreads();
-    if (!last_cta) return;
-    __threadfence();
-    select_stump(J, cnt);
+    for (int c = kRescanSplitCap + (int)blockIdx.x; c < cnt; c += (int)gridDim.x) {
+        const Candidate cd = rescan_feature(J, J.cand_ids[c], rres);
+        if (threadIdx.x == 0) {
+            J.cands[c] = cd;
+            __threadfence();
+            last_cta = atomicAdd(&rs->done_rescan, 1u) == (uint32_t)cnt - 1;
+        }
+        __syncthreads();
+        if (last_cta && warp == 0) {
+            __threadfence();
+            select_stump_warp(J, cnt, lane);
+        }
+        __syncthreads();
+    }
 }
 
 cudaError_t launch_rescan(const JobDesc &J, int grid, cudaStream_t st) {
-    k_rescan<<<grid, kRescanWarps * 32, 0, st>>>(J);
+    (void)grid;
+    k_rescan<<<kRescanCtas, kRescanCtaWarps * 32, 0, st>>>(J);
     return cudaGetLastError();
 }
 

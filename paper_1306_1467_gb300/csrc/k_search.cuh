@@ -260,73 +260,119 @@ static __device__ RunResult rescan_run(const uint16_t *__restrict__ row, int run
     return r;
 }
 
-// The whole CTA (kRescanWarps warps) re-scans feature f of job J; thread 0
-// returns its best (error, split, polarity).  `rres` is 32 slots of shared memory.
+// One warp combines a row's 32 lane runs (lane k holds run k's result q):
+// runs in value order, an exclusive double-float scan of their totals places
+// each run's extremes in the row; then the largest and the smallest prefix
+// over the row (lowest split on ties), split 0 (D = 0) included, give the
+// feature's best error, split and polarity.  The result is valid in lane 0.
+__device__ __forceinline__ Candidate combine_runs(const JobDesc &J, int32_t f, const RunResult &q, int lane) {
+    Candidate cd;
+    cd.err_hi = INFINITY; cd.err_lo = 0.f; cd.feature = f; cd.split = 0; cd.polarity = 1; cd.pad = 0;
+    DF x = q.total;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const DF y = df_shfl_up(x, d);
+        if (lane >= d) x = df_add(y, x);
+    }
+    DF offs = df_shfl_up(x, 1);
+    if (lane == 0) offs = DF{0.f, 0.f};
+    DF bmax = q.smx != INT_MAX ? df_add(offs, q.mx) : DF{-INFINITY, 0.f};
+    DF bmn = q.smn != INT_MAX ? df_add(offs, q.mn) : DF{INFINITY, 0.f};
+    int smax = q.smx, smn = q.smn;
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        const DF om = df_shfl_xor(bmax, d);
+        const int os = __shfl_xor_sync(0xffffffffu, smax, d);
+        if (df_less(bmax, om) || (df_eq(om, bmax) && os < smax)) { bmax = om; smax = os; }
+        const DF on = df_shfl_xor(bmn, d);
+        const int on_s = __shfl_xor_sync(0xffffffffu, smn, d);
+        if (df_less(on, bmn) || (df_eq(on, bmn) && on_s < smn)) { bmn = on; smn = on_s; }
+    }
+    if (!df_less(DF{0.f, 0.f}, bmax)) { bmax = DF{0.f, 0.f}; smax = 0; }
+    if (!df_less(bmn, DF{0.f, 0.f})) { bmn = DF{0.f, 0.f}; smn = 0; }
+    if (lane == 0) {
+        const DF Tp = df_from_double(J.rs->t_pos), Tm = df_from_double(J.rs->t_neg);
+        const DF ep = df_add(Tp, df_neg(bmax));
+        const DF em = df_add(Tm, bmn);
+        const bool minus = df_less(em, ep) || (df_eq(em, ep) && smn < smax);
+        cd.err_hi = minus ? em.hi : ep.hi;
+        cd.err_lo = minus ? em.lo : ep.lo;
+        cd.split = minus ? smn : smax;
+        cd.polarity = minus ? -1 : 1;
+    }
+    return cd;
+}
+
+// The whole CTA re-scans feature f of job J, its warps taking the row's 32
+// lane runs in turn; thread 0 returns its best (error, split, polarity).
+// `rres` is 32 slots of shared memory.
 static __device__ Candidate rescan_feature(const JobDesc &J, int32_t f, RunResult *rres) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
     const int run = J.npad / 32;
     const uint16_t *row = J.rows + (size_t)f * J.npad;
-    for (int k = warp; k < 32; k += kRescanWarps) {
+    for (int k = warp; k < 32; k += nw) {
         const RunResult r = rescan_run(row, run, k, J.v, lane);
         if (lane == 0) rres[k] = r;
     }
     __syncthreads();
     Candidate cd;
     cd.err_hi = INFINITY; cd.err_lo = 0.f; cd.feature = f; cd.split = 0; cd.polarity = 1; cd.pad = 0;
-    if (warp == 0) {
-        // runs in value order: an exclusive double-float scan of their totals
-        // places each run's extremes in the row; then the largest and the
-        // smallest prefix over the row (lowest split on ties), split 0 (D = 0)
-        // included
-        const RunResult q = rres[lane];
-        DF x = q.total;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const DF y = df_shfl_up(x, d);
-            if (lane >= d) x = df_add(y, x);
-        }
-        DF offs = df_shfl_up(x, 1);
-        if (lane == 0) offs = DF{0.f, 0.f};
-        DF bmax = q.smx != INT_MAX ? df_add(offs, q.mx) : DF{-INFINITY, 0.f};
-        DF bmn = q.smn != INT_MAX ? df_add(offs, q.mn) : DF{INFINITY, 0.f};
-        int smax = q.smx, smn = q.smn;
-#pragma unroll
-        for (int d = 16; d; d >>= 1) {
-            const DF om = df_shfl_xor(bmax, d);
-            const int os = __shfl_xor_sync(0xffffffffu, smax, d);
-            if (df_less(bmax, om) || (df_eq(om, bmax) && os < smax)) { bmax = om; smax = os; }
-            const DF on = df_shfl_xor(bmn, d);
-            const int on_s = __shfl_xor_sync(0xffffffffu, smn, d);
-            if (df_less(on, bmn) || (df_eq(on, bmn) && on_s < smn)) { bmn = on; smn = on_s; }
-        }
-        if (!df_less(DF{0.f, 0.f}, bmax)) { bmax = DF{0.f, 0.f}; smax = 0; }
-        if (!df_less(bmn, DF{0.f, 0.f})) { bmn = DF{0.f, 0.f}; smn = 0; }
-        if (lane == 0) {
-            const DF Tp = df_from_double(J.rs->t_pos), Tm = df_from_double(J.rs->t_neg);
-            const DF ep = df_add(Tp, df_neg(bmax));
-            const DF em = df_add(Tm, bmn);
-            const bool minus = df_less(em, ep) || (df_eq(em, ep) && smn < smax);
-            cd.err_hi = minus ? em.hi : ep.hi;
-            cd.err_lo = minus ? em.lo : ep.lo;
-            cd.split = minus ? smn : smax;
-            cd.polarity = minus ? -1 : 1;
-        }
-    }
+    if (warp == 0) cd = combine_runs(J, f, rres[lane], lane);
     __syncthreads();
     return cd;
+}
+
+// The round's stump from the best of `cnt` re-scanned candidates, `b` (one
+// thread); no candidate stops the job with an error flag.
+__device__ __forceinline__ void record_stump(const JobDesc &J, int cnt, const Candidate &b) {
+    RoundState *rs = J.rs;
+    if (cnt == 0 || b.feature == INT_MAX) {
+        rs->flags |= kFlagNoCandidate;
+        rs->status = VJB_EDEVICE;
+    } else {
+        rs->win_feature = b.feature;
+        rs->win_split = b.split;
+        rs->win_polarity = b.polarity;
+        rs->win_err_hi = b.err_hi;
+        rs->win_err_lo = b.err_lo;
+    }
+    rs->done_rescan = 0u;
+}
+
+__device__ __forceinline__ Candidate load_candidate(const Candidate *p) {
+    Candidate c;
+    const volatile Candidate *vc = p;
+    c.err_hi = vc->err_hi; c.err_lo = vc->err_lo; c.feature = vc->feature;
+    c.split = vc->split; c.polarity = vc->polarity; c.pad = 0;
+    return c;
+}
+
+// One warp picks job J's stump among its `cnt` re-scanned candidates.
+__device__ __forceinline__ void select_stump_warp(const JobDesc &J, int cnt, int lane) {
+    Candidate b;
+    b.err_hi = INFINITY; b.err_lo = 0.f; b.feature = INT_MAX; b.split = INT_MAX; b.polarity = 1; b.pad = 0;
+    for (int k = lane; k < cnt; k += 32) {
+        const Candidate c = load_candidate(J.cands + k);
+        if (cand_less(c, b)) b = c;
+    }
+#pragma unroll
+    for (int d = 16; d; d >>= 1) {
+        const Candidate o = cand_shfl_xor(b, d);
+        if (cand_less(o, b)) b = o;
+    }
+    if (lane == 0) record_stump(J, cnt, b);
 }
 
 // The whole CTA picks job J's stump among its `cnt` re-scanned candidates.
 static __device__ void select_stump(const JobDesc &J, int cnt) {
     __shared__ Candidate wc[kRescanWarps];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nw = blockDim.x >> 5;
     Candidate b;
     b.err_hi = INFINITY; b.err_lo = 0.f; b.feature = INT_MAX; b.split = INT_MAX; b.polarity = 1; b.pad = 0;
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-        Candidate c;
-        const volatile Candidate *vc = J.cands + k;
-        c.err_hi = vc->err_hi; c.err_lo = vc->err_lo; c.feature = vc->feature;
-        c.split = vc->split; c.polarity = vc->polarity; c.pad = 0;
+        const Candidate c = load_candidate(J.cands + k);
         if (cand_less(c, b)) b = c;
     }
 #pragma unroll
@@ -337,27 +383,14 @@ static __device__ void select_stump(const JobDesc &J, int cnt) {
     if (lane == 0) wc[warp] = b;
     __syncthreads();
     if (warp == 0) {
-        b = wc[lane];  // kRescanWarps == 32
+        if (lane < nw) b = wc[lane];
 #pragma unroll
         for (int d = 16; d; d >>= 1) {
             const Candidate o = cand_shfl_xor(b, d);
             if (cand_less(o, b)) b = o;
         }
     }
-    if (threadIdx.x == 0) {
-        RoundState *rs = J.rs;
-        if (cnt == 0 || b.feature == INT_MAX) {
-            rs->flags |= kFlagNoCandidate;
-            rs->status = VJB_EDEVICE;
-        } else {
-            rs->win_feature = b.feature;
-            rs->win_split = b.split;
-            rs->win_polarity = b.polarity;
-            rs->win_err_hi = b.err_hi;
-            rs->win_err_lo = b.err_lo;
-        }
-        rs->done_rescan = 0u;
-    }
+    if (threadIdx.x == 0) record_stump(J, cnt, b);
     __syncthreads();
 }
 

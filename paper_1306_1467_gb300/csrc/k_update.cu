@@ -96,18 +96,25 @@ int update_grid(int n) {
     return g < 1 ? 1 : (g > kUpdateMaxCtas ? kUpdateMaxCtas : g);
 }
 
-// Per-CTA reduction of three doubles into partials[3 * blk + k].
-__device__ __forceinline__ void cta_partials(double a, double b, double c, double *partials, int blk) {
+// Per-CTA reduction of three doubles into partials[3 * blk + k].  FP64 runs
+// at a couple of lanes per clock per SM on this GPU, so a warp-wide FP64 add
+// costs a dozen or more cycles: the third value is reduced only where it can
+// be non-zero (`third`, uniform over the launch), and its slot is 0 otherwise.
+__device__ __forceinline__ void cta_partials(double a, double b, double c, bool third, double *partials, int blk) {
     __shared__ double red[3][kUpdateThreads / 32];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     a = warp_sum_d(a);
     b = warp_sum_d(b);
-    c = warp_sum_d(c);
+    if (third) c = warp_sum_d(c);
     if (lane == 0) { red[0][wp] = a; red[1][wp] = b; red[2][wp] = c; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        for (int k = 0; k < kUpdateThreads / 32; ++k) { s0 += red[0][k]; s1 += red[1][k]; s2 += red[2][k]; }
+        for (int k = 0; k < kUpdateThreads / 32; ++k) {
+            s0 += red[0][k];
+            s1 += red[1][k];
+            if (third) s2 += red[2][k];
+        }
         partials[3 * blk + 0] = s0;
         partials[3 * blk + 1] = s1;
         partials[3 * blk + 2] = s2;
@@ -163,30 +170,45 @@ __device__ void update_a_block(const JobDesc &J, int blk) {
         tw = wi;
         if (m) mw = wi;
     }
-    cta_partials(mw, tw, below, J.partials, blk);
+    cta_partials(mw, tw, below, forced, J.partials, blk);
 }
 
-// Sums of the three per-block partials over `nblocks` blocks, by the whole
-// finishing CTA in a fixed order (strided per thread, then the CTA); every
-// thread gets them.
-__device__ __forceinline__ void sum_partials(const double *partials, int nblocks, double &a, double &b,
-                                             double &c) {
+// Sums of the three per-block partials over `nblocks` blocks by the finishing
+// CTA in a fixed order (strided per thread, each warp, then the warps in
+// order by one thread); every thread gets them.  The third only where it can
+// be non-zero (`third`), as in cta_partials.
+__device__ __forceinline__ void sum_partials(const double *partials, int nblocks, bool third, double &a,
+                                             double &b, double &c) {
     __shared__ double red[3][kUpdateThreads / 32];
+    __shared__ double tot[3];
     double x = 0.0, y = 0.0, z = 0.0;
     for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
         x += ((volatile const double *)partials)[3 * k + 0];
         y += ((volatile const double *)partials)[3 * k + 1];
-        z += ((volatile const double *)partials)[3 * k + 2];
+        if (third) z += ((volatile const double *)partials)[3 * k + 2];
     }
     x = warp_sum_d(x);
     y = warp_sum_d(y);
-    z = warp_sum_d(z);
+    if (third) z = warp_sum_d(z);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     __syncthreads();
     if (lane == 0) { red[0][wp] = x; red[1][wp] = y; red[2][wp] = z; }
     __syncthreads();
-    a = b = c = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { a += red[0][k]; b += red[1][k]; c += red[2][k]; }
+    if (threadIdx.x == 0) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            s0 += red[0][k];
+            s1 += red[1][k];
+            if (third) s2 += red[2][k];
+        }
+        tot[0] = s0;
+        tot[1] = s1;
+        tot[2] = s2;
+    }
+    __syncthreads();
+    a = tot[0];
+    b = tot[1];
+    c = tot[2];
 }
 
 // The searched stump's canonical threshold: p=+1 -> value at position s
@@ -211,67 +233,79 @@ __device__ void store_threshold(const JobDesc &J) {
     rs->win_theta = theta;
 }
 
-// Step 3-4, part 1, finish (thread 0, after every block; the CTA's threads
-// have summed the partials): the stump's FP64 error, threshold, beta and
-// alpha, its record, and the update factors.
+// Step 3-4, part 1, finish (after every block; the CTA's threads have summed
+// the partials): the stump's FP64 error, threshold, beta and alpha, its
+// record, and the update factors.  Three warps share the scalar work, so that
+// the factors update b waits for do not queue behind the logarithm, the
+// divisions of the diagnostics and their memory traffic (one thread did all of
+// it in 7.5 us of a 13.3 us update at 24x24 / 15k): warp 0 the factors and
+// the round state, warp 1 alpha and the stump record, warp 2 the diagnostics.
+// Each value is computed exactly as one thread would.
 __device__ void update_a_finish(const JobDesc &J, double M, double T, double B) {
     RoundState *rs = J.rs;
+    // the round state the parts read, taken before any part writes it
     const bool forced = rs->forced != 0;
     const int32_t f = forced ? rs->forced_feature : rs->win_feature;
     const int32_t p = forced ? rs->forced_polarity : rs->win_polarity;
     const int32_t s = forced ? 0 : rs->win_split;
+    const int32_t r0 = rs->rounds;
+    const int32_t cands = rs->cand_count;
+    __syncthreads();
     const double eps = M / T;
-    int32_t theta, split = s;
-    if (forced) {
-        theta = rs->forced_threshold;
-        split = (int32_t)B;
-    } else {
-        // written by another CTA in this launch: read past this SM's L1
-        theta = *reinterpret_cast<volatile int32_t *>(&rs->win_theta);
-    }
-    vjb_stump st;
-    st.feature = f;
-    st.threshold = theta;
-    st.polarity = p;
-    st.split = split;
-    st.error = eps;
-    // what the search saw of this stump, next to its FP64 error; the search
-    // works in units of the current weight total T, so divide by it
-    vjb_round_diag dg;
-    dg.search_error = forced ? eps : ((double)rs->win_err_hi + (double)rs->win_err_lo) / T;
-    dg.screen_error = forced ? (float)eps : (float)((double)J.ferr[f] / T);
-    dg.screen_min = forced ? (float)eps : (float)((double)rs->screen_min / T);
-    dg.candidates = forced ? 0 : rs->cand_count;
-    dg.forced = forced ? 1 : 0;
-    if (rs->rounds < J.stump_cap) J.diag[rs->rounds] = dg;
-    rs->last_cands = rs->cand_count;
-    rs->cand_count = 0;
-    rs->forced = 0;
-    rs->done_update_a = 0u;
-    if (eps == 0.0) {
-        // perfect stump: kept with alpha = +inf, training is over
-        st.beta = 0.0;
-        st.alpha = INFINITY;
-        if (rs->rounds < J.stump_cap) J.stumps[rs->rounds] = st;
-        rs->rounds += 1;
+    if (threadIdx.x == 0) {
+        rs->last_cands = cands;
+        rs->cand_count = 0;
+        rs->forced = 0;
+        rs->done_update_a = 0u;
+        if (eps == 0.0) {
+            // perfect stump: kept with alpha = +inf, training is over
+            rs->rounds = r0 + 1;
+            rs->status = VJB_DONE_PERFECT;
+        } else if (eps >= 0.5) {
+            // no stump does better than chance: not kept, training is over
+            rs->status = VJB_DONE_NOGAIN;
+        } else {
+            const double beta = eps / (1.0 - eps);
+            rs->rounds = r0 + 1;
+            const double Z = M + beta * (T - M);
+            rs->scale_hit = beta / Z;
+            rs->scale_miss = 1.0 / Z;
+        }
+    } else if (threadIdx.x == 32) {
+        int32_t theta, split = s;
+        if (forced) {
+            theta = rs->forced_threshold;
+            split = (int32_t)B;
+        } else {
+            // written by another CTA in this launch: read past this SM's L1
+            theta = *reinterpret_cast<volatile int32_t *>(&rs->win_theta);
+        }
+        vjb_stump st;
+        st.feature = f;
+        st.threshold = theta;
+        st.polarity = p;
+        st.split = split;
+        st.error = eps;
+        if (eps == 0.0) {
+            st.beta = 0.0;
+            st.alpha = INFINITY;
+        } else {
+            st.beta = eps / (1.0 - eps);
+            st.alpha = log((1.0 - eps) / eps);  // log(1 / beta)
+        }
         *J.last = st;
-        rs->status = VJB_DONE_PERFECT;
-        return;
+        if (eps < 0.5 && r0 < J.stump_cap) J.stumps[r0] = st;
+    } else if (threadIdx.x == 64) {
+        // what the search saw of this stump, next to its FP64 error; the search
+        // works in units of the current weight total T, so divide by it
+        vjb_round_diag dg;
+        dg.search_error = forced ? eps : ((double)rs->win_err_hi + (double)rs->win_err_lo) / T;
+        dg.screen_error = forced ? (float)eps : (float)((double)J.ferr[f] / T);
+        dg.screen_min = forced ? (float)eps : (float)((double)rs->screen_min / T);
+        dg.candidates = forced ? 0 : cands;
+        dg.forced = forced ? 1 : 0;
+        if (r0 < J.stump_cap) J.diag[r0] = dg;
     }
-    const double beta = eps / (1.0 - eps);
-    st.beta = beta;
-    st.alpha = log((1.0 - eps) / eps);  // log(1 / beta)
-    *J.last = st;
-    if (eps >= 0.5) {
-        // no stump does better than chance: not kept, training is over
-        rs->status = VJB_DONE_NOGAIN;
-        return;
-    }
-    if (rs->rounds < J.stump_cap) J.stumps[rs->rounds] = st;
-    rs->rounds += 1;
-    const double Z = M + beta * (T - M);
-    rs->scale_hit = beta / Z;
-    rs->scale_miss = 1.0 / Z;
 }
 
 // Step 4 and step 1 of the next round for the 256 samples of block `blk`.
@@ -286,7 +320,7 @@ __device__ void update_b_block(const JobDesc &J, int blk) {
         store_v(J.v, J.lay, i, face ? fw : -fw);
         if (face) tp = (double)fw; else tn = (double)fw;
     }
-    cta_partials(tp, tn, 0.0, J.partials, blk);
+    cta_partials(tp, tn, 0.0, false, J.partials, blk);
 }
 
 __device__ void update_b_finish(const JobDesc &J, double P, double Q) {
@@ -300,13 +334,15 @@ __device__ void update_b_finish(const JobDesc &J, double P, double Q) {
 // The finishing CTA of update a / update b (all its threads).
 __device__ void finish_a(const JobDesc &J, int nblocks) {
     double M, T, B;
-    sum_partials(J.partials, nblocks, M, T, B);
-    if (threadIdx.x == 0) update_a_finish(J, M, T, B);
+    // (the count below the threshold only for a host-given stump; read before
+    // any part of the finish resets `forced`)
+    sum_partials(J.partials, nblocks, J.rs->forced != 0, M, T, B);
+    update_a_finish(J, M, T, B);
 }
 
 __device__ void finish_b(const JobDesc &J, int nblocks) {
     double P, Q, unused;
-    sum_partials(J.partials, nblocks, P, Q, unused);
+    sum_partials(J.partials, nblocks, false, P, Q, unused);
     if (threadIdx.x == 0) update_b_finish(J, P, Q);
 }
 

@@ -186,6 +186,8 @@ JobDesc job_desc(const vjb_ctx *c) {
     J.rs = c->d_rs;
     J.ferr = c->d_ferr;
     J.cand_ids = c->d_cand_ids;
+    J.runres = static_cast<RunResult *>(c->d_runres);
+    J.cand_runs = c->d_cand_runs;
     J.cands = c->d_cand;
     J.stumps = c->d_stumps;
     J.diag = c->d_diag;
@@ -402,6 +404,11 @@ int prepare_tables(vjb_ctx *c) {
     if (!c->d_ferr) CK(cudaMalloc(&c->d_ferr, sizeof(float) * c->nfeat));
     if (!c->d_cand) CK(cudaMalloc(&c->d_cand, sizeof(Candidate) * c->nfeat));
     if (!c->d_cand_ids) CK(cudaMalloc(&c->d_cand_ids, sizeof(int32_t) * c->nfeat));
+    if (!c->d_runres) CK(cudaMalloc(&c->d_runres, (size_t)kRunResultBytes * 32 * kRescanSplitCap));
+    if (!c->d_cand_runs) {
+        CK(cudaMalloc(&c->d_cand_runs, sizeof(uint32_t) * kRescanSplitCap));
+        CK(cudaMemset(c->d_cand_runs, 0, sizeof(uint32_t) * kRescanSplitCap));
+    }
     if (!c->d_bmin || !c->tmap_ok) {
         rc = choose_default_shape(c);
         if (rc) return rc;

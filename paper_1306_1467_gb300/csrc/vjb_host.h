@@ -94,6 +94,8 @@ struct vjb_ctx {
     float *d_ferr = nullptr, *d_bmin = nullptr;
     Candidate *d_cand = nullptr;
     int32_t *d_cand_ids = nullptr;
+    void *d_runres = nullptr;        // re-scan: lane-run results of the split features
+    uint32_t *d_cand_runs = nullptr;  // re-scan: runs done per split feature (kept at zero between rounds)
     uint8_t *d_miss = nullptr;
     int32_t *d_scratch = nullptr;  // table preparation: check state and listed rows
     double *d_partials = nullptr;
@@ -136,7 +138,7 @@ struct vjb_ctx {
         dfree(d_rows);
         rows_external = false;
         dfree(d_w); dfree(d_v); dfree(d_wtmp); dfree(d_ferr); dfree(d_bmin); dfree(d_cand);
-        dfree(d_cand_ids); dfree(d_miss); dfree(d_partials); dfree(d_scratch);
+        dfree(d_cand_ids); dfree(d_runres); dfree(d_cand_runs); dfree(d_miss); dfree(d_partials); dfree(d_scratch);
         dfree(d_rs); dfree(d_stumps); dfree(d_last); dfree(d_diag);
         stump_cap = bmin_cap = 0;
         feats.clear();

@@ -126,6 +126,12 @@ __host__ __device__ __forceinline__ bool entry_flag(uint32_t e, int phys) {
 // compensated.  It is twice a bound on the screening error (see k_search.cu).
 constexpr float kScreenMarginUlps = 72.0f;
 
+// The plain re-scan spreads the first kRescanSplitCap shortlisted features'
+// lane runs over the grid, one run per warp; later ones (a tie plateau) are
+// re-scanned whole by one CTA each.  A run result is 32 bytes.
+constexpr int kRescanSplitCap = 256;
+constexpr int kRunResultBytes = 32;
+
 // Partials of the multi-CTA update kernels (one slot per CTA).
 constexpr int kUpdateThreads = 256;
 constexpr int kUpdateMaxCtas = 4096;
@@ -147,6 +153,8 @@ struct JobDesc {
     float *ferr;
     int32_t *cand_ids;
     struct Candidate *cands;
+    struct RunResult *runres;  // plain re-scan: lane-run results [kRescanSplitCap][32]
+    uint32_t *cand_runs;       // plain re-scan: runs done per candidate [kRescanSplitCap]
     vjb_stump *stumps;
     vjb_round_diag *diag;
     vjb_stump *last;
