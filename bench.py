@@ -32,7 +32,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "boosting rounds/s at 24x24, 15k samples"
 STUMP_BYTES = 40
-PROFILE = os.path.join(ROOT, "profiles", "k_screen_paper_24x24_15k.txt")
+PROFILE_DIR = os.path.join(ROOT, "profiles")
 SEARCH_SRC = os.path.join(ROOT, "paper_1306_1467_gb300", "csrc", "k_search.cu")
 FALLBACK_HBM_GBS = 6800.0
 
@@ -96,13 +96,14 @@ def search_source_digest() -> str:
     return hashlib.sha256((shared + src[a:b] + dev).encode()).hexdigest()
 
 
-def _traffic():
-    """DRAM bytes per search launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+def _traffic(workload: str = "paper_24x24_15k"):
+    """DRAM bytes per search launch from the committed ncu summary of this
+    workload (profiles/k_screen_<workload>.txt), if it was taken on the
+    current kernel source."""
     try:
         sha = search_source_digest()
         kv = {}
-        for line in open(PROFILE):
+        for line in open(os.path.join(PROFILE_DIR, f"k_screen_{workload}.txt")):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
@@ -386,7 +387,7 @@ def run_ours(a, ws, rank, local):
     avg_search_ms = tm["search_ms_total"] / max(tm["rounds"], 1)
     achieved = search_bytes / (avg_search_ms / 1000.0) / 1e9
     peak, peak_src = _peak()
-    traffic = _traffic()
+    traffic = _traffic(a.workload)
     line = {
         "metric": METRIC, "value": value, "unit": "rounds/s", "n_gpus": ws, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,

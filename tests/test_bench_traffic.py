@@ -15,12 +15,12 @@ if ROOT not in sys.path:
 import bench  # noqa: E402
 
 
-def _summary(tmp_path, sha, nbytes="4.9065e9"):
-    p = tmp_path / "k_screen.txt"
+def _summary(tmp_path, sha, nbytes="4.9065e9", workload="paper_24x24_15k"):
+    p = tmp_path / f"k_screen_{workload}.txt"
     p.write_text("# header line: with a colon\n"
                  f"dram_bytes_per_launch: {nbytes}\n"
                  f"source_sha256: {sha}\n")
-    return str(p)
+    return str(tmp_path)
 
 
 def test_committed_summary_is_plausible():
@@ -34,17 +34,23 @@ def test_committed_summary_is_plausible():
 
 
 def test_traffic_is_read_for_the_current_source(tmp_path, monkeypatch):
-    monkeypatch.setattr(bench, "PROFILE", _summary(tmp_path, bench.search_source_digest()))
+    monkeypatch.setattr(bench, "PROFILE_DIR", _summary(tmp_path, bench.search_source_digest()))
     assert bench._traffic() == 4.9065e9
 
 
+def test_traffic_is_only_the_profiled_workloads(tmp_path, monkeypatch):
+    # a summary of the 24x24 / 15k table says nothing about another workload's
+    monkeypatch.setattr(bench, "PROFILE_DIR", _summary(tmp_path, bench.search_source_digest()))
+    assert bench._traffic("search_16x16_15k") is None
+
+
 def test_traffic_is_null_once_the_kernel_changed(tmp_path, monkeypatch):
-    monkeypatch.setattr(bench, "PROFILE", _summary(tmp_path, "0" * 64))
+    monkeypatch.setattr(bench, "PROFILE_DIR", _summary(tmp_path, "0" * 64))
     assert bench._traffic() is None
 
 
 def test_traffic_is_null_without_a_summary(tmp_path, monkeypatch):
-    monkeypatch.setattr(bench, "PROFILE", str(tmp_path / "missing.txt"))
+    monkeypatch.setattr(bench, "PROFILE_DIR", str(tmp_path / "missing"))
     assert bench._traffic() is None
 
 
