@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
         const JobDesc &J = jobs[W.job];
         if (!J.rs->in_round) continue;
         if (W.job != cur_job) {  // this job's weights into shared memory
-            for (int i = threadIdx.x; i < J.lay.words; i += blockDim.x) sv[i] = J.v[i];
+            stage_weights(sv, J.v, J.lay.words);
             __syncthreads();
             cur_job = W.job;
         }
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
             for (int w = 0; w < nw; ++w) m = fminf(m, s_min[w]);
             if (m < INFINITY) atomicMin(&jobs[prev].rs->screen_min_bits, __float_as_uint(fmaxf(m, 0.f)));
         }
-        for (int i = threadIdx.x; i < J.lay.words; i += blockDim.x) sv[i] = J.v[i];
+        stage_weights(sv, J.v, J.lay.words);
         __syncthreads();
         prev = j;
         const int lines = J.lines;
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
             for (int w = 0; w < nw; ++w) m = fminf(m, s_min[w]);
             if (m < INFINITY) atomicMin(&jobs[prev].rs->screen_min_bits, __float_as_uint(fmaxf(m, 0.f)));
         }
-        for (int i = threadIdx.x; i < J.lay.words; i += blockDim.x) sv[i] = J.v[i];
+        stage_weights(sv, J.v, J.lay.words);
         __syncthreads();
         prev = j;
         const int lines = J.lines;

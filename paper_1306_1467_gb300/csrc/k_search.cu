@@ -88,14 +88,12 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
     const uint32_t bars0 = ring0 + (uint32_t)nw * stages * stage_bytes;
     float *wbest = reinterpret_cast<float *>(reinterpret_cast<char *>(sv) + (bars0 + nw * stages * 8 - sv32));
 
-    for (int i = threadIdx.x; i < words; i += blockDim.x) sv[i] = v[i];
     const uint32_t ring_w = ring0 + (uint32_t)warp * stages * stage_bytes;
     const uint32_t bar_w = bars0 + (uint32_t)(warp * stages * 8);
     if (lane == 0) {
         for (int s = 0; s < stages; ++s) mbar_init(bar_w + 8 * s, 1);
         fence_barrier_init();
     }
-    __syncthreads();
 
     // rows gw, gw + G, ... of this warp; feature indices fit int32 (nfeat <
     // 2^31), and so does the warp's chunk count (G >= 152 warps, at most 128
@@ -122,6 +120,9 @@ __global__ void __launch_bounds__(U >= 4 ? 384 : (U == 3 ? 512 : 640), 1)
     if (lane == 0)
         for (int s = 0; s < stages; ++s) issue_next();
     __syncwarp();
+    // the weights, staged while the first copies of the table are in flight
+    stage_weights(sv, v, words);
+    __syncthreads();
 
     const float Tp = (float)rs->t_pos, Tm = (float)rs->t_neg;
     float best = INFINITY;
