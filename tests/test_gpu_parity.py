@@ -364,6 +364,39 @@ def test_paper_shape_full_round_parity(paper_gpu):
         assert abs(w_gpu.sum() - 1.0) < 1e-6
 
 
+def test_precision_form_paper_shape():
+    """The precision form at its own shape: 24x24, 15,000 windows, all 162,336
+    features, weights drawn log-uniformly in [1e-12, 1] (max / min about 1e12).
+    Three rounds, each on the GPU's own FP32 weights of that round: the FP64
+    error within 1e-6 of the oracle's search over every feature, the stump the
+    oracle's unless its two best errors lie within 1e-6; the compensated
+    (double-float) search error of the stump within 1e-9 of its FP64 error;
+    every FP32 screened error within the screening bound of the oracle's."""
+    from paper_1306_1467_gb300 import vjb
+    px, y, _ = synth.workload("precision_24x24_15k")
+    with _trainer() as tr:
+        feats = tr.prepare(px, y)
+        tr.set_weights(synth.log_uniform_weights(y.shape[0], seed=1308))
+        w0 = tr.get_weights().astype(np.float64)
+        assert w0.max() / w0[w0 > 0].min() > 1e11
+        stumps = []
+        for t in range(3):
+            wn = O.normalize(tr.get_weights().astype(np.float64))
+            best = _oracle_best_streaming(px, y, feats, wn)
+            ref = O.select(best)
+            st, s = tr.train_round()
+            assert st == vjb.OK
+            assert abs(s["error"] - ref["err"]) <= REL * ref["err"], (t, s, ref)
+            if ref["second_err"] - ref["err"] > REL * ref["err"]:
+                assert (s["feature"], s["threshold"], s["polarity"]) == (ref["feature"], ref["threshold"], ref["polarity"])
+            ferr = tr.screen_errors().astype(np.float64)
+            assert np.max(np.abs(ferr - best["err"])) <= SCREEN_TOL, t
+            stumps.append(s)
+        for s, d in zip(stumps, tr.round_diag()):
+            assert d["forced"] == 0 and d["candidates"] >= 1
+            assert abs(d["search_error"] - s["error"]) <= 1e-9 * s["error"]
+
+
 def test_precision_form_mid_size():
     """Precision form at 16x16 / 3000 windows (32,384 features): weights
     log-uniform in [1e-12, 1].  Each round on the same FP32 weights: the FP64
