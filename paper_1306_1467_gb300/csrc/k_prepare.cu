@@ -483,12 +483,17 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
     __syncthreads();
 
     const uint32_t lt = lanemask_lt();
-    // one stable pass over the D-bit digit at value bit `shift`
+    // one stable pass over the D-bit digit at value bit `shift`; the sorted
+    // items end in skey and in c
     auto radix_pass = [&](auto dbits, int shift) {
         constexpr int D = decltype(dbits)::value;
         constexpr uint32_t DMASK = (1u << D) - 1u;
+        // counts warp-major (warp w's digit d at w * R + d): the lanes of a
+        // warp touch neighbouring words, whatever their digits
+        constexpr int R = (1 << D) + (sizeof(HT) == 2 ? 2 : 1);
+        static_assert(WARPS * R <= HWORDS, "histogram space too small");
         const int sh = ib + shift;
-        for (int k = threadIdx.x; k < (1 << D) * HSTRIDE; k += TH) hist[k] = 0;
+        for (int k = threadIdx.x; k < WARPS * R; k += TH) hist[k] = 0;
         __syncthreads();
         // each item's rank among the warp's earlier items of its digit, in
         // position order (item j before item j + 1, lanes in order): in shared
@@ -501,8 +506,8 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
             const int leader = __ffs(peers) - 1;
             uint32_t old = 0;
             if (lane == leader) {
-                old = hist[dg * HSTRIDE + wp];
-                hist[dg * HSTRIDE + wp] = (HT)(old + __popc(peers));
+                old = hist[wp * R + dg];
+                hist[wp * R + dg] = (HT)(old + __popc(peers));
             }
             old = __shfl_sync(0xffffffffu, old, leader) + __popc(peers & lt);
             if constexpr (RS) {
@@ -521,7 +526,7 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
                 const int lin = threadIdx.x * PER + q;
-                cnt[q] = hist[(lin / WARPS) * HSTRIDE + (lin % WARPS)];
+                cnt[q] = hist[(lin % WARPS) * R + lin / WARPS];
                 s += cnt[q];
             }
             // CTA-wide exclusive scan of the per-thread sums
@@ -548,7 +553,7 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
 #pragma unroll
             for (int q = 0; q < PER; ++q) {
                 const int lin = threadIdx.x * PER + q;
-                hist[(lin / WARPS) * HSTRIDE + (lin % WARPS)] = (HT)off;
+                hist[(lin % WARPS) * R + lin / WARPS] = (HT)off;
                 off += cnt[q];
             }
         }
@@ -557,12 +562,12 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
         for (int j = 0; j < IPT; ++j) {
             const uint32_t dg = (c[j] >> sh) & DMASK;
             const uint32_t r = RS ? (uint32_t)rks[pos0 + j * 32] : ((rk[j >> 1] >> (16 * (j & 1))) & 0xffffu);
-            skey[hist[dg * HSTRIDE + wp] + r] = c[j];
+            skey[hist[wp * R + dg] + r] = c[j];
         }
         __syncthreads();
+        // the next pass's first write to skey or hist follows two barriers
 #pragma unroll
         for (int j = 0; j < IPT; ++j) c[j] = skey[pos0 + j * 32];
-        __syncthreads();
     };
     // Two passes at most (value bits <= 18); the digit is as narrow as that
     // allows (one ballot per digit bit), at least 5 bits.
@@ -578,10 +583,12 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
                 default: radix_pass(std::integral_constant<int, kPkDigitBits>{}, shift); break;
             }
         }
-    }
+    } else {
+        // one value: the items are already in order
 #pragma unroll
-    for (int j = 0; j < IPT; ++j) skey[pos0 + j * 32] = c[j];
-    __syncthreads();
+        for (int j = 0; j < IPT; ++j) skey[pos0 + j * 32] = c[j];
+        __syncthreads();
+    }
 
     uint16_t *out = rows + (size_t)blockIdx.x * npad;
     const int run = npad / 32;
