@@ -16,28 +16,35 @@ namespace vjb {
 // so that the feature kernel reads consecutive windows with coalesced loads.
 // ii(x, y) = sum of pixels with x' < x and y' < y (zero first row and column),
 // built row by row: ii(x, y) = ii(x, y - 1) + (sum of row y - 1 up to x - 1).
+// With ii16 non-null, also the values modulo 2^16 in the same layout (the
+// sort evaluates features of small boxes from these).
 __global__ void k_integral(const uint8_t *__restrict__ px, int n, int h, int w,
-                           int32_t *__restrict__ ii_t, int stride) {
+                           int32_t *__restrict__ ii_t, uint16_t *__restrict__ ii16, int stride) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int W1 = w + 1;
     const uint8_t *img = px + (size_t)i * h * w;
-    for (int x = 0; x <= w; ++x) ii_t[(size_t)x * stride + i] = 0;
+    for (int x = 0; x <= w; ++x) {
+        ii_t[(size_t)x * stride + i] = 0;
+        if (ii16) ii16[(size_t)x * stride + i] = 0;
+    }
     for (int y = 1; y <= h; ++y) {
         ii_t[(size_t)(y * W1) * stride + i] = 0;
+        if (ii16) ii16[(size_t)(y * W1) * stride + i] = 0;
         int32_t row = 0;
         for (int x = 1; x <= w; ++x) {
             row += img[(y - 1) * w + (x - 1)];
             const int32_t up = ii_t[(size_t)((y - 1) * W1 + x) * stride + i];
             ii_t[(size_t)(y * W1 + x) * stride + i] = up + row;
+            if (ii16) ii16[(size_t)(y * W1 + x) * stride + i] = (uint16_t)(up + row);
         }
     }
 }
 
-cudaError_t launch_integral(const uint8_t *px, int n, int h, int w, int32_t *ii_t, int ii_stride,
-                            cudaStream_t st) {
+cudaError_t launch_integral(const uint8_t *px, int n, int h, int w, int32_t *ii_t, uint16_t *ii16,
+                            int ii_stride, cudaStream_t st) {
     const int b = 128;
-    k_integral<<<(n + b - 1) / b, b, 0, st>>>(px, n, h, w, ii_t, ii_stride);
+    k_integral<<<(n + b - 1) / b, b, 0, st>>>(px, n, h, w, ii_t, ii16, ii_stride);
     return cudaGetLastError();
 }
 
@@ -413,7 +420,7 @@ __host__ __device__ constexpr bool packed_ranks_in_smem(int ipt, int th) { retur
 
 template <int IPT, int TH>
 __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
-    k_sort_rows_packed(const int32_t *__restrict__ ii_t, int ii_stride, int w,
+    k_sort_rows_packed(const int32_t *__restrict__ ii_t, const uint16_t *__restrict__ ii16, int ii_stride, int w,
                        const DevFeature *__restrict__ feat, int64_t f0, WeightLayout L,
                        uint16_t *__restrict__ rows, int npad, int32_t *ovf, int32_t *stat) {
     constexpr int NP = TH * IPT;
@@ -442,18 +449,25 @@ __global__ void __launch_bounds__(TH, TH <= 512 ? 2 : 1)
     const DevFeature d = feat[f0 + blockIdx.x];
 
     // the feature on every window (K2's arithmetic), four windows per thread
-    // and corner load
+    // and corner load; boxes of at most kNarrowArea pixels from the integral
+    // images modulo 2^16 (half the bytes)
     int32_t lo = INT_MAX, hi = INT_MIN;
-    for (int q = threadIdx.x; 4 * q < n; q += TH) {
-        const int p = 4 * q;
-        const int4 x = haar_value4(ii_t, ii_stride, w, d.type, d.x, d.y, d.w, d.h, p);
-        reinterpret_cast<uint4 *>(skey)[q] = make_uint4((uint32_t)x.x, (uint32_t)x.y, (uint32_t)x.z, (uint32_t)x.w);
-        lo = min(lo, x.x);
-        hi = max(hi, x.x);
-        if (p + 1 < n) { lo = min(lo, x.y); hi = max(hi, x.y); }
-        if (p + 2 < n) { lo = min(lo, x.z); hi = max(hi, x.z); }
-        if (p + 3 < n) { lo = min(lo, x.w); hi = max(hi, x.w); }
-    }
+    auto values = [&](auto value4) {
+        for (int q = threadIdx.x; 4 * q < n; q += TH) {
+            const int p = 4 * q;
+            const int4 x = value4(p);
+            reinterpret_cast<uint4 *>(skey)[q] = make_uint4((uint32_t)x.x, (uint32_t)x.y, (uint32_t)x.z, (uint32_t)x.w);
+            lo = min(lo, x.x);
+            hi = max(hi, x.x);
+            if (p + 1 < n) { lo = min(lo, x.y); hi = max(hi, x.y); }
+            if (p + 2 < n) { lo = min(lo, x.z); hi = max(hi, x.z); }
+            if (p + 3 < n) { lo = min(lo, x.w); hi = max(hi, x.w); }
+        }
+    };
+    if (ii16 && d.w * d.h <= kNarrowArea)
+        values([&](int p) { return haar_value4_narrow(ii16, ii_stride, w, d.type, d.x, d.y, d.w, d.h, p); });
+    else
+        values([&](int p) { return haar_value4(ii_t, ii_stride, w, d.type, d.x, d.y, d.w, d.h, p); });
 #pragma unroll
     for (int s = 16; s; s >>= 1) {
         lo = min(lo, __shfl_xor_sync(0xffffffffu, lo, s));
@@ -706,15 +720,16 @@ static size_t sort_packed_smem() {
 }
 
 template <int IPT, int TH = kPkThreads>
-static cudaError_t launch_sort_packed(const int32_t *ii_t, int ii_stride, int w, const DevFeature *feat,
+static cudaError_t launch_sort_packed(const int32_t *ii_t, const uint16_t *ii16, int ii_stride, int w,
+                                      const DevFeature *feat,
                                       int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows,
                                       int npad, int32_t *ovf, int32_t *stat, cudaStream_t st) {
     const size_t sm = sort_packed_smem<IPT, TH>();
     cudaError_t e = cudaFuncSetAttribute(k_sort_rows_packed<IPT, TH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    k_sort_rows_packed<IPT, TH><<<(unsigned)nf, TH, sm, st>>>(ii_t, ii_stride, w, feat, f0, L, rows, npad, ovf,
-                                                              stat);
+    k_sort_rows_packed<IPT, TH><<<(unsigned)nf, TH, sm, st>>>(ii_t, ii16, ii_stride, w, feat, f0, L, rows, npad,
+                                                              ovf, stat);
     return cudaGetLastError();
 }
 
@@ -736,21 +751,21 @@ static cudaError_t launch_sort_wide(const int32_t *ii_t, int ii_stride, int w, c
 // Rows of a tile: the packed sort for every row (512 threads up to 16,384
 // samples, 1024 above), then the two-word sort for the rows whose value span
 // and sample index do not fit one word, which the packed sort lists.
-// `scratch` (3 + nf ints of device memory): [0] and [1] the table's check
+// `ii16` (the integral images modulo 2^16, or null) serves the packed sort's
+// features of small boxes.  `scratch` (3 + nf ints of device memory): [0] and [1] the table's check
 // state (see row_written; zeroed by the caller once per table), [2] the
 // tile's listed-row count, then the listed rows.  Waits for the stream when
 // it reads the count.
-cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, const DevFeature *feat,
-                             int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows, int npad,
-                             int32_t *scratch, cudaStream_t st) {
-    (void)h;
+cudaError_t launch_sort_rows(const int32_t *ii_t, const uint16_t *ii16, int ii_stride, int w,
+                             const DevFeature *feat, int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows,
+                             int npad, int32_t *scratch, cudaStream_t st) {
     if (nf <= 0) return cudaSuccess;
     const int n = L.n;
     int32_t *stat = scratch, *ovf = scratch + 2;
     cudaError_t e = cudaMemsetAsync(ovf, 0, sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
     if (n <= kPkThreads * 32) {
-#define VJB_PK_CASE(I) launch_sort_packed<I>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, ovf, stat, st)
+#define VJB_PK_CASE(I) launch_sort_packed<I>(ii_t, ii16, ii_stride, w, feat, f0, nf, L, rows, npad, ovf, stat, st)
         const int ipt = (n + kPkThreads - 1) / kPkThreads;
         if (ipt <= 4) e = VJB_PK_CASE(4);
         else if (ipt <= 8) e = VJB_PK_CASE(8);
@@ -764,7 +779,7 @@ cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, c
 #undef VJB_PK_CASE
     } else {
 #define VJB_PK_WIDE(I) \
-    launch_sort_packed<I, 1024>(ii_t, ii_stride, w, feat, f0, nf, L, rows, npad, ovf, stat, st)
+    launch_sort_packed<I, 1024>(ii_t, ii16, ii_stride, w, feat, f0, nf, L, rows, npad, ovf, stat, st)
         const int ipt = (n + 1023) / 1024;
         if (ipt <= 20) e = VJB_PK_WIDE(20);
         else if (ipt <= 24) e = VJB_PK_WIDE(24);

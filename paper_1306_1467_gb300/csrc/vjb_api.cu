@@ -396,7 +396,7 @@ int prepare_tables(vjb_ctx *c) {
     cudaError_t e = cudaMemsetAsync(d_scratch, 0, 2 * sizeof(int32_t), c->stream);
     for (int64_t f0 = 0; f0 < c->nfeat && e == cudaSuccess; f0 += tile) {
         const int64_t nf = std::min(tile, c->nfeat - f0);
-        e = launch_sort_rows(c->d_ii, c->ii_stride, c->w, c->h, c->d_feat, f0, nf, c->lay,
+        e = launch_sort_rows(c->d_ii, c->ii16(), c->ii_stride, c->w, c->d_feat, f0, nf, c->lay,
                              c->d_rows + (size_t)f0 * c->npad, c->npad, d_scratch, c->stream);
         c->launches += 1;
     }
@@ -501,11 +501,13 @@ int vjb_build_integral(vjb_ctx *c) {
     if (c->stage < kStageLoaded) return fail(VJB_ESTATE, "vjb_build_integral before vjb_load_windows");
     int rc = set_dev(c);
     if (rc) return rc;
+    // the int32 integral images, then the same modulo 2^16 (ii16())
     if (!c->d_ii) {
         c->ii_stride = (c->n + 31) / 32 * 32;
-        CK(cudaMalloc(&c->d_ii, sizeof(int32_t) * (size_t)(c->h + 1) * (c->w + 1) * c->ii_stride));
+        CK(cudaMalloc(&c->d_ii, (sizeof(int32_t) + sizeof(uint16_t)) * (size_t)(c->h + 1) * (c->w + 1) *
+                                    c->ii_stride));
     }
-    CK(launch_integral(c->d_px, c->n, c->h, c->w, c->d_ii, c->ii_stride, c->stream));
+    CK(launch_integral(c->d_px, c->n, c->h, c->w, c->d_ii, c->ii16(), c->ii_stride, c->stream));
     c->launches += 1;
     CK(cudaStreamSynchronize(c->stream));
     c->stage = kStageIntegral;
@@ -734,7 +736,7 @@ int vjb_classify(vjb_ctx *c, const uint8_t *pixels, int32_t n, const vjb_stump *
     if (e == cudaSuccess && scores) e = cudaMalloc(&d_sc, sizeof(double) * (size_t)n);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_px, pixels, px_bytes, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess && T > 0) e = cudaMemcpyAsync(d_st, stumps, sizeof(vjb_stump) * T, cudaMemcpyHostToDevice, c->stream);
-    if (e == cudaSuccess) e = launch_integral(d_px, n, c->h, c->w, d_ii, stride, c->stream);
+    if (e == cudaSuccess) e = launch_integral(d_px, n, c->h, c->w, d_ii, nullptr, stride, c->stream);
     if (e == cudaSuccess)
         e = launch_strong_classify(d_ii, stride, n, c->w, c->d_feat, d_st, T, half, d_lab, d_sc, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(labels, d_lab, (size_t)n, cudaMemcpyDeviceToHost, c->stream);

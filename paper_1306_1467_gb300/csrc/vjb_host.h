@@ -148,6 +148,10 @@ struct vjb_ctx {
         nfeat = 0;
         lay = WeightLayout{};
     }
+    // the integral images modulo 2^16, stored after the int32 ones in d_ii
+    uint16_t *ii16() const {
+        return d_ii ? reinterpret_cast<uint16_t *>(d_ii + (size_t)(h + 1) * (w + 1) * ii_stride) : nullptr;
+    }
     void free_events() {
         for (auto &t : ev_free) for (auto e : t) cudaEventDestroy(e);
         for (auto &t : ev_pending) for (auto e : t.ev) cudaEventDestroy(e);

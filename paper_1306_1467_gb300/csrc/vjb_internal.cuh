@@ -206,17 +206,17 @@ size_t search_smem_bytes(const SearchShape &s, int words);
 WeightLayout make_layout(int n, bool allow_dual);
 
 // Launchers (each returns the launch error).
-cudaError_t launch_integral(const uint8_t *px, int n, int h, int w, int32_t *ii_t, int ii_stride,
-                            cudaStream_t st);
+cudaError_t launch_integral(const uint8_t *px, int n, int h, int w, int32_t *ii_t, uint16_t *ii16,
+                            int ii_stride, cudaStream_t st);
 cudaError_t launch_strong_classify(const int32_t *ii_t, int ii_stride, int n, int win_w, const DevFeature *feat,
                                    const vjb_stump *stumps, int T, double half_alpha, uint8_t *labels,
                                    double *scores, cudaStream_t st);
 cudaError_t launch_feature_values(const int32_t *ii_t, int ii_stride, int n, int w,
                                   const DevFeature *feat, int64_t f0, int64_t nf, int32_t *out,
                                   cudaStream_t st);
-cudaError_t launch_sort_rows(const int32_t *ii_t, int ii_stride, int w, int h, const DevFeature *feat,
-                             int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows, int npad,
-                             int32_t *scratch, cudaStream_t st);
+cudaError_t launch_sort_rows(const int32_t *ii_t, const uint16_t *ii16, int ii_stride, int w,
+                             const DevFeature *feat, int64_t f0, int64_t nf, const WeightLayout &L, uint16_t *rows,
+                             int npad, int32_t *scratch, cudaStream_t st);
 cudaError_t launch_init_weights(const uint8_t *y, const WeightLayout &L, const float *w_in,
                                 float *w, float *v, RoundState *rs, cudaStream_t st);
 cudaError_t launch_screen(const CUtensorMap *tmap, const float *v, const WeightLayout &L,

@@ -570,3 +570,47 @@ def test_sort_18_bit_spans_packed():
         tr.prepare(px, y)
         for k, f in enumerate(picks):
             _check_rows(tr.sorted_rows(f, 1), vals[k:k + 1], order[k:k + 1])
+
+
+def test_sort_small_boxes_at_their_value_extremes():
+    """Features whose box holds at most 257 pixels are evaluated from the
+    integral images modulo 2^16: their values span at most 255 * 257 = 65535
+    integers, so the residue names one value.  18x18 windows of black and
+    white halves, thirds and quadrants (both polarities), all black, all white
+    and random black/white pixels drive these features to both ends of their
+    range (asserted for boxes of 250 pixels and more, two- and
+    three-rectangle types); every row, the larger boxes (int32 images)
+    included, bit for bit against the oracle's stable order."""
+    from paper_1306_1467_gb300 import vjb
+    rng = np.random.Generator(np.random.PCG64(1309))
+    side = 18
+    pats = [np.zeros((side, side), np.uint8), np.full((side, side), 255, np.uint8)]
+    grid = np.indices((side, side))
+    for axis in (0, 1):
+        c = grid[axis]
+        pats += [np.where(c < side // 2, 255, 0), np.where(c < side // 2, 0, 255)]
+        for k in range(3):  # one third white, the rest black, and the inverse
+            band = (c >= k * side // 3) & (c < (k + 1) * side // 3)
+            pats += [np.where(band, 255, 0), np.where(band, 0, 255)]
+    quad = (grid[0] < side // 2) ^ (grid[1] < side // 2)
+    pats += [np.where(quad, 255, 0), np.where(quad, 0, 255)]
+    pats = np.stack(pats).astype(np.uint8)
+    n = 4000
+    px = (rng.random((n, side, side)) < 0.5).astype(np.uint8) * 255
+    px[: 40 * len(pats)] = np.repeat(pats, 40, axis=0)
+    px = px[rng.permutation(n)]
+    y = (rng.random(n) < 0.4).astype(np.uint8)
+    desc, _ = O.haar_enumerate(side, side)
+    vals = O.feature_values(px, desc)
+    order = O.sort_rows(vals)
+    t, fw, fh = desc[:, 0], desc[:, 3].astype(np.int64), desc[:, 4].astype(np.int64)
+    three = (t == vjb.HAAR_TYPES.index("3H")) | (t == vjb.HAAR_TYPES.index("3V"))
+    neg = np.where(three, 2 * fw * fh // 3, fw * fh // 2)
+    small = fw * fh <= 257
+    ends = (vals.min(axis=1) == -255 * neg) & (vals.max(axis=1) == 255 * (fw * fh - neg))
+    assert 0 < (~small).sum() and small.mean() > 0.9
+    for kind in (three, ~three):
+        assert (ends & small & kind & (fw * fh >= 250)).any()
+    with _trainer() as tr:
+        assert np.array_equal(tr.prepare(px, y), desc)
+        _check_rows(tr.sorted_rows(0, desc.shape[0]), vals, order)
