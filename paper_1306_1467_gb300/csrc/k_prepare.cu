@@ -7,6 +7,7 @@
 #include <type_traits>
 
 #include "vjb_device.cuh"
+#include "vjb_haar.cuh"
 #include "vjb_internal.cuh"
 
 namespace vjb {
