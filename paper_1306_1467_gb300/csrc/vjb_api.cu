@@ -385,10 +385,11 @@ int prepare_tables(vjb_ctx *c) {
         CK(cudaMalloc(&c->d_rows, sizeof(uint16_t) * (size_t)c->nfeat * c->npad));
     }
     // feature values (the K2 arithmetic, fused into the sort) and sort, a tile
-    // of rows per launch; the sort kernels check every entry they write (the
-    // search kernels gather through the table without bounds checks) and
-    // count the rows they write
-    const int64_t tile = std::max<int64_t>(1, std::min<int64_t>(c->nfeat, 65535));
+    // of rows per launch (one launch up to 2^22 rows: 24x24 windows take one,
+    // so no SM idles at a tile's end); the sort kernels check every entry they
+    // write (the search kernels gather through the table without bounds
+    // checks) and count the rows they write
+    const int64_t tile = std::max<int64_t>(1, std::min<int64_t>(c->nfeat, int64_t(1) << 22));
     // (kept with the context: a cudaFree here would wait for the whole device,
     // other contexts' rounds included, when a server prepares a request)
     if (!c->d_scratch) CK(cudaMalloc(&c->d_scratch, sizeof(int32_t) * (size_t)(3 + tile)));
