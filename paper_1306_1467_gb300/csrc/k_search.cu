@@ -243,11 +243,23 @@ int screen_occupancy(const SearchShape &s, int words) {
 __global__ void __launch_bounds__(256)
     k_shortlist(const JobDesc J, const float *__restrict__ bmin, int nbmin) {
     RoundState *rs = J.rs;
-    if (rs->status != VJB_OK || rs->forced) return;
     __shared__ float red[8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t b0 = (int64_t)blockIdx.x * blockDim.x + warp * 32;
+    // every load this kernel needs before it can decide, issued together: the
+    // thread's first screened errors, the per-CTA minima and the round state
+    // (three dependent trips to memory were a third of the kernel)
+    constexpr int kPre = 3;
+    float fe[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+        const int64_t f = b0 + q * stride + lane;
+        fe[q] = f < J.nfeat ? J.ferr[f] : INFINITY;
+    }
     float m = INFINITY;
     for (int i = threadIdx.x; i < nbmin; i += blockDim.x) m = fminf(m, bmin[i]);
+    if (rs->status != VJB_OK || rs->forced) return;
     m = warp_min(m);
     if (lane == 0) red[warp] = m;
     __syncthreads();
@@ -255,17 +267,21 @@ __global__ void __launch_bounds__(256)
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fminf(m, red[w]);
     const float thr = shortlist_threshold(m, rs);
     if (blockIdx.x == 0 && threadIdx.x == 0) rs->screen_min = m;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + warp * 32; base < J.nfeat; base += stride) {
+    auto step = [&](int64_t base, float e) {  // base: uniform over the warp
         const int64_t f = base + lane;
-        const bool take = f < J.nfeat && J.ferr[f] <= thr;
+        const bool take = f < J.nfeat && e <= thr;
         const uint32_t mask = __ballot_sync(0xffffffffu, take);
-        if (!mask) continue;
+        if (!mask) return;
         int slot0 = 0;
         if (lane == 0) slot0 = atomicAdd(&rs->cand_count, __popc(mask));
         slot0 = __shfl_sync(0xffffffffu, slot0, 0);
         if (take) J.cand_ids[slot0 + __popc(mask & ((1u << lane) - 1u))] = (int32_t)f;
-    }
+    };
+#pragma unroll
+    for (int q = 0; q < kPre; ++q)
+        if (b0 + q * stride < J.nfeat) step(b0 + q * stride, fe[q]);
+    for (int64_t base = b0 + kPre * stride; base < J.nfeat; base += stride)
+        step(base, base + lane < J.nfeat ? J.ferr[base + lane] : INFINITY);
 }
 
 cudaError_t launch_shortlist(const JobDesc &J, const float *bmin, int nbmin, int grid, cudaStream_t st) {

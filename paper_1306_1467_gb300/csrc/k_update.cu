@@ -138,15 +138,21 @@ __device__ __forceinline__ bool last_block_done(uint32_t *counter, int nblocks) 
 
 // Step 3-4, part 1, for the 256 samples (or sorted positions) of block `blk`:
 // e_i and the block's FP64 sums of misclassified weight, of all weight and (for
-// a host-given stump) of samples below the threshold.
-__device__ void update_a_block(const JobDesc &J, int blk) {
+// a host-given stump) of samples below the threshold.  The round state's
+// fields are read in one trip with the status; false (nothing done, uniform
+// over the CTA) when the job has stopped or, in a batch, sits this round out.
+__device__ bool update_a_block(const JobDesc &J, int blk, bool batched) {
     const int n = J.lay.n;
     const RoundState *rs = J.rs;
-    const bool forced = rs->forced != 0;
-    const int32_t f = forced ? rs->forced_feature : rs->win_feature;
-    const int32_t p = forced ? rs->forced_polarity : rs->win_polarity;
-    const int32_t s = forced ? 0 : rs->win_split;
+    const int32_t status = rs->status, in_round = rs->in_round, forced_i = rs->forced;
+    const int32_t ff = rs->forced_feature, wf = rs->win_feature;
+    const int32_t fp = rs->forced_polarity, wp = rs->win_polarity, ws = rs->win_split;
     const int32_t theta_f = rs->forced_threshold;
+    if (status != VJB_OK || (batched && !in_round)) return false;
+    const bool forced = forced_i != 0;
+    const int32_t f = forced ? ff : wf;
+    const int32_t p = forced ? fp : wp;
+    const int32_t s = forced ? 0 : ws;
     const int k = blk * kUpdateThreads + threadIdx.x;
     double mw = 0.0, tw = 0.0, below = 0.0;
     if (k < n) {
@@ -172,6 +178,7 @@ __device__ void update_a_block(const JobDesc &J, int blk) {
         if (m) mw = wi;
     }
     cta_partials(mw, tw, below, forced, J.partials, blk);
+    return true;
 }
 
 // Sums of the three per-block partials over `nblocks` blocks by the finishing
@@ -309,19 +316,29 @@ __device__ void update_a_finish(const JobDesc &J, double M, double T, double B) 
     }
 }
 
-// Step 4 and step 1 of the next round for the 256 samples of block `blk`.
-__device__ void update_b_block(const JobDesc &J, int blk) {
+// Step 4 and step 1 of the next round for the 256 samples of block `blk`.  The
+// samples' miss flags, weights and labels are read in the same trip as the
+// round state; false as for update_a_block.
+__device__ bool update_b_block(const JobDesc &J, int blk, bool batched) {
     const int i = blk * kUpdateThreads + threadIdx.x;
+    const bool in = i < J.lay.n;
+    const bool miss = in && J.miss[i];
+    const float w0 = in ? J.w[i] : 0.f;
+    const bool face = in && J.y[i] != 0;
+    const RoundState *rs = J.rs;
+    const int32_t status = rs->status, in_round = rs->in_round;
+    const double scale_miss = rs->scale_miss, scale_hit = rs->scale_hit;
+    if (status != VJB_OK || (batched && !in_round)) return false;
     double tp = 0.0, tn = 0.0;
-    if (i < J.lay.n) {
-        const double scale = J.miss[i] ? J.rs->scale_miss : J.rs->scale_hit;
-        const float fw = __double2float_rn((double)J.w[i] * scale);
+    if (in) {
+        const double scale = miss ? scale_miss : scale_hit;
+        const float fw = __double2float_rn((double)w0 * scale);
         J.w[i] = fw;
-        const bool face = J.y[i] != 0;
         store_v(J.v, J.lay, i, face ? fw : -fw);
         if (face) tp = (double)fw; else tn = (double)fw;
     }
     cta_partials(tp, tn, 0.0, false, J.partials, blk);
+    return true;
 }
 
 __device__ void update_b_finish(const JobDesc &J, double P, double Q) {
@@ -348,16 +365,14 @@ __device__ void finish_b(const JobDesc &J, int nblocks) {
 }
 
 __global__ void __launch_bounds__(kUpdateThreads) k_update_a(const JobDesc J) {
-    if (J.rs->status != VJB_OK) return;
-    update_a_block(J, blockIdx.x);
+    if (!update_a_block(J, blockIdx.x, false)) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) store_threshold(J);
     if (!last_block_done(&J.rs->done_update_a, gridDim.x)) return;
     finish_a(J, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kUpdateThreads) k_update_b(const JobDesc J) {
-    if (J.rs->status != VJB_OK) return;
-    update_b_block(J, blockIdx.x);
+    if (!update_b_block(J, blockIdx.x, false)) return;
     if (!last_block_done(&J.rs->done_update_b, gridDim.x)) return;
     finish_b(J, gridDim.x);
 }
@@ -393,12 +408,11 @@ __global__ void __launch_bounds__(kUpdateThreads) k_bupdate(const JobDesc *__res
         }
         const JobDesc &J = jobs[lo];
         const int blk = g - base[lo], nblocks = base[lo + 1] - base[lo];
-        if (!J.rs->in_round || J.rs->status != VJB_OK) continue;
         if (A) {
-            update_a_block(J, blk);
+            if (!update_a_block(J, blk, true)) continue;
             if (blk == 0 && threadIdx.x == 0) store_threshold(J);
         } else {
-            update_b_block(J, blk);
+            if (!update_b_block(J, blk, true)) continue;
         }
         if (last_block_done(A ? &J.rs->done_update_a : &J.rs->done_update_b, nblocks)) {
             if (A) finish_a(J, nblocks);
