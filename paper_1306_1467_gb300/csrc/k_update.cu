@@ -99,26 +99,27 @@ int update_grid(int n) {
 
 // Per-CTA reduction of three doubles into partials[3 * blk + k].  FP64 runs
 // at a couple of lanes per clock per SM on this GPU, so a warp-wide FP64 add
-// costs a dozen or more cycles: the third value is reduced only where it can
-// be non-zero (`third`, uniform over the launch), and its slot is 0 otherwise.
+// takes the FP64 pipe of its scheduler for tens of cycles: each value is
+// summed by a warp of its own (warps 0, 1, 2 sit on different schedulers),
+// lane l adding the threads l, l + 32, ... in order and the lanes then by a
+// butterfly, 13 warp-wide adds a value instead of 40 spread over the CTA.
+// The third value is reduced only where it can be non-zero (`third`, uniform
+// over the launch), and its slot is 0 otherwise.
 __device__ __forceinline__ void cta_partials(double a, double b, double c, bool third, double *partials, int blk) {
-    __shared__ double red[3][kUpdateThreads / 32];
+    __shared__ double red[3][kUpdateThreads];
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    a = warp_sum_d(a);
-    b = warp_sum_d(b);
-    if (third) c = warp_sum_d(c);
-    if (lane == 0) { red[0][wp] = a; red[1][wp] = b; red[2][wp] = c; }
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    if (third) red[2][threadIdx.x] = c;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        for (int k = 0; k < kUpdateThreads / 32; ++k) {
-            s0 += red[0][k];
-            s1 += red[1][k];
-            if (third) s2 += red[2][k];
+    if (wp < 3) {
+        double x = 0.0;
+        if (wp < 2 || third) {
+#pragma unroll
+            for (int k = 0; k < kUpdateThreads / 32; ++k) x += red[wp][lane + 32 * k];
+            x = warp_sum_d(x);
         }
-        partials[3 * blk + 0] = s0;
-        partials[3 * blk + 1] = s1;
-        partials[3 * blk + 2] = s2;
+        if (lane == 0) partials[3 * blk + wp] = x;
     }
 }
 
@@ -182,36 +183,21 @@ __device__ bool update_a_block(const JobDesc &J, int blk, bool batched) {
 }
 
 // Sums of the three per-block partials over `nblocks` blocks by the finishing
-// CTA in a fixed order (strided per thread, each warp, then the warps in
-// order by one thread); every thread gets them.  The third only where it can
-// be non-zero (`third`), as in cta_partials.
+// CTA in a fixed order, each value by a warp of its own (lane l adds blocks
+// l, l + 32, ... in order, then the lanes by a butterfly); every thread gets
+// them.  The third only where it can be non-zero (`third`), as in
+// cta_partials.
 __device__ __forceinline__ void sum_partials(const double *partials, int nblocks, bool third, double &a,
                                              double &b, double &c) {
-    __shared__ double red[3][kUpdateThreads / 32];
     __shared__ double tot[3];
-    double x = 0.0, y = 0.0, z = 0.0;
-    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) {
-        x += ((volatile const double *)partials)[3 * k + 0];
-        y += ((volatile const double *)partials)[3 * k + 1];
-        if (third) z += ((volatile const double *)partials)[3 * k + 2];
-    }
-    x = warp_sum_d(x);
-    y = warp_sum_d(y);
-    if (third) z = warp_sum_d(z);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) { red[0][wp] = x; red[1][wp] = y; red[2][wp] = z; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            s0 += red[0][k];
-            s1 += red[1][k];
-            if (third) s2 += red[2][k];
+    if (wp < 3) {
+        double x = 0.0;
+        if (wp < 2 || third) {
+            for (int k = lane; k < nblocks; k += 32) x += ((volatile const double *)partials)[3 * k + wp];
+            x = warp_sum_d(x);
         }
-        tot[0] = s0;
-        tot[1] = s1;
-        tot[2] = s2;
+        if (lane == 0) tot[wp] = x;
     }
     __syncthreads();
     a = tot[0];
