@@ -338,6 +338,19 @@ __global__ void __launch_bounds__(kRescanCtaWarps * 32) k_rescan(const JobDesc J
         // this feature's last run: combine its 32 runs
         __threadfence();
         const Candidate cd = combine_runs(J, f, load_run_result(J.runres + c * 32 + lane), lane);
+        if (cnt == 1) {
+            // the only listed feature (most rounds): the stump, picked as the
+            // list would pick it, without the trip through the list
+            if (lane == 0) {
+                J.cand_runs[c] = 0u;
+                Candidate b;
+                b.err_hi = INFINITY; b.err_lo = 0.f; b.feature = INT_MAX; b.split = INT_MAX; b.polarity = 1;
+                b.pad = 0;
+                if (cand_less(cd, b)) b = cd;
+                record_stump(J, 1, b);
+            }
+            continue;
+        }
         uint32_t done = 0;
         if (lane == 0) {
             J.cand_runs[c] = 0u;
