@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(256)
     const int64_t b0 = (int64_t)blockIdx.x * blockDim.x + warp * 32;
     // every load this kernel needs before it can decide, issued together: the
     // thread's first screened errors, the per-CTA minima and the round state
-    // (three dependent trips to memory were a third of the kernel)
+    // (one trip to memory instead of three in a row: 4.2 instead of 5.5 us a
+    // launch at 24x24 / 15k under ncu, with the updates' same change)
     constexpr int kPre = 3;
     float fe[kPre];
 #pragma unroll
